@@ -1,0 +1,122 @@
+"""Pins for the oracle's reductions (C7).
+
+The exact-sum oracle (a long fixed-point accumulator) is checked against
+Python's math.fsum, which returns the correctly rounded sum of its doubles
+(Shewchuk's algorithm): an independent library routine.  Integer sums are
+checked against Python big integers reduced mod 2^64.
+"""
+import math
+import random
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2106_03219_gb300 import inputs
+
+
+def fsum32(a):
+    return math.fsum(np.asarray(a, dtype=np.float32).astype(np.float64).tolist())
+
+
+@pytest.mark.parametrize("gen", ["pm1", "lognormal", "uniform01"])
+def test_exact_sum_vs_fsum(gen):
+    n = 1 << 16
+    a = {"pm1": inputs.f32_uniform_pm1, "lognormal": inputs.f32_lognormal_signed,
+         "uniform01": inputs.f32_uniform01}[gen](n, 3)
+    assert O.exact_sum_f32(a) == fsum32(a)
+
+
+def test_exact_sum_vs_fsum_million_slice():
+    a = inputs.f32_uniform_pm1(1 << 20, 0)
+    assert O.exact_sum_f32(a) == fsum32(a)
+
+
+def test_exact_sum_order_independent():
+    a = inputs.f32_lognormal_signed(50000, 11)
+    ref = O.exact_sum_f32(a)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        b = a.copy()
+        rng.shuffle(b)
+        assert O.exact_sum_f32(b) == ref
+
+
+def test_exact_sum_hand_cases():
+    f = np.float32
+    assert O.exact_sum_f32(np.array([1e8, 1, -1e8], f)) == 1.0
+    assert O.exact_sum_f32(np.array([], f)) == 0.0
+    # ties to even: 1 + 2^-53 rounds to 1; 1 + 3*2^-53 rounds up to 1 + 2^-51
+    assert O.exact_sum_f32(np.array([1.0, 2.0 ** -53], f)) == 1.0
+    assert O.exact_sum_f32(np.array([1.0, 2.0 ** -53, 2.0 ** -52], f)) == 1.0 + 2.0 ** -51
+    # just above the tie rounds up
+    assert O.exact_sum_f32(np.array([1.0, 2.0 ** -53, 2.0 ** -80], f)) == 1.0 + 2.0 ** -52
+    # subnormals and the top of the range
+    tiny = np.float32(1e-45)
+    assert O.exact_sum_f32(np.array([tiny, tiny, -tiny], f)) == float(tiny)
+    big = np.float32(3e38)
+    assert O.exact_sum_f32(np.array([big, big, big, -big], f)) == 2 * float(big)
+    # exact cancellation to zero
+    a = inputs.f32_uniform_pm1(1000, 1)
+    assert O.exact_sum_f32(np.concatenate([a, -a])) == 0.0
+
+
+def test_exact_sum_mixed_dynamic_range():
+    rng = np.random.default_rng(9)
+    e = rng.integers(-149, 127, size=20000)
+    m = rng.uniform(1.0, 2.0, size=20000) * np.where(rng.random(20000) < 0.5, -1, 1)
+    a = np.ldexp(m, e).astype(np.float32)
+    a = a[np.isfinite(a)]
+    assert O.exact_sum_f32(a) == fsum32(a)
+
+
+def test_exact_dot_vs_fsum():
+    x = inputs.f32_uniform01(30000, 0)
+    y = inputs.f32_uniform01(30000, 1)
+    ref = math.fsum((x.astype(np.float64) * y.astype(np.float64)).tolist())
+    assert O.exact_dot_f32(x, y) == ref
+    # extreme products: subnormal x subnormal and near-overflow squared
+    x = np.array([1e-45, 3e38, -3e38, 1.0], np.float32)
+    y = np.array([1e-45, 3e38, 3e38, 2.0 ** -149], np.float32)
+    ref = math.fsum((x.astype(np.float64) * y.astype(np.float64)).tolist())
+    assert O.exact_dot_f32(x, y) == ref
+
+
+def test_exact_sum_bf16_vs_fsum():
+    bits = inputs.bf16_uniform_pm1(40000, 2)
+    vals = (bits.astype(np.uint32) << 16).view(np.float32)
+    assert O.exact_sum_bf16(bits) == fsum32(vals)
+
+
+def test_exact_sum_f64_combine():
+    rng = random.Random(4)
+    vals = [rng.uniform(-1e6, 1e6) for _ in range(5000)]
+    assert O.exact_sum_f64(np.array(vals)) == math.fsum(vals)
+
+
+def test_abs_sum():
+    a = inputs.f32_uniform_pm1(10000, 5)
+    assert O.exact_abs_sum_f32(a) == math.fsum(np.abs(a.astype(np.float64)).tolist())
+
+
+def test_int_sums_wrap():
+    a = inputs.int64_uniform(10000, 3)
+    assert O.sum_int(a) == sum(int(v) for v in a)
+    big = np.array([(1 << 63) - 1, 5, (1 << 63) - 2, -(1 << 63)], np.int64)
+    s = sum(int(v) for v in big) % (1 << 64)
+    s = s - (1 << 64) if s >= (1 << 63) else s
+    assert O.sum_int(big) == s
+    x = inputs.int32_uniform(10000, 0)
+    assert O.sum_int(x) == sum(int(v) for v in x)
+
+
+def test_max_min():
+    for a in (inputs.f32_uniform_pm1(5000, 1), inputs.f32_lognormal_signed(5000, 2)):
+        assert O.max_min(a, "max") == float(max(a.tolist()))
+        assert O.max_min(a, "min") == float(min(a.tolist()))
+    b = inputs.int64_uniform(5000, 3)
+    assert O.max_min(b, "max") == max(b.tolist())
+    assert O.max_min(b, "min") == min(b.tolist())
+    c = inputs.int32_uniform(5000, 4)
+    assert O.max_min(c, "max") == max(c.tolist())
+    assert O.max_min(c, "min") == min(c.tolist())
