@@ -1,0 +1,339 @@
+/*
+ * omprt.h - C ABI of a GB300-native (sm_103a) OpenMP device-runtime hot path.
+ *
+ * The paper ("Experience Report: Writing A Portable GPU Runtime with OpenMP
+ * 5.1", arXiv 2106.03219) describes the LLVM OpenMP device runtime: the
+ * routines an offloaded region calls on the GPU, among them the division of
+ * loop iterations (Sec. 1, Sec. 2), __kmpc_alloc_shared (Sec. 2.1, Listing 1),
+ * team-shared state with one team per thread block (Sec. 3.1, "Global Shared
+ * Variables"), the flush and the five atomics (Sec. 3.1, Listings 2-3) and
+ * synchronisation / thread hierarchy (Sec. 3.2).  This library provides the
+ * data-parallel subset of those routines that a
+ *     #pragma omp target teams distribute parallel for [reduction(...)]
+ * loop spends its time in, as hand-written CUDA kernels, behind plain C calls.
+ * The host launch call plays the role of the host runtime's target-launch
+ * entry (Sec. 2.2: kernel id, base pointers, argument count).
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev or held in descriptors are DEVICE pointers owned
+ *     by the caller; the library never frees them.  Pointers named *_host are
+ *     host memory.  The context (omprt_ctx) owns only its own scratch.
+ *   - stream is a CUDA stream handle (cudaStream_t / CUstream) passed as
+ *     void*; NULL means the legacy default stream.  Every launch is
+ *     asynchronous on that stream.
+ *   - Host-side argument errors return a non-OK status immediately and launch
+ *     nothing.  Errors detected on the device set bits in a sticky device
+ *     status word that omprt_sync_status reads and clears.  No call throws or
+ *     traps.
+ *   - Calls that launch work allocate nothing after omprt_init (and after
+ *     omprt_batch_create for the batch call), so they may be captured in a
+ *     CUDA graph.
+ *   - A context's scratch (cross-team partials, tickets, dispatch counters)
+ *     is handed out from a ring of OMPRT_SLOTS slots, one per launch; up to
+ *     OMPRT_SLOTS launches from one context may be in flight at once on
+ *     different streams.  Replays of a captured graph reuse the slots baked
+ *     into it, so one captured graph must not be replayed concurrently with
+ *     itself.
+ */
+#ifndef OMPRT_H_
+#define OMPRT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OMPRT_SLOTS 64
+/* teams of a launch that reduces or uses dynamic dispatch */
+#define OMPRT_MAX_RED_TEAMS 16384
+/* fallback-pool bytes per team for the shared-memory stack */
+#define OMPRT_POOL_BYTES_PER_TEAM 4096
+
+typedef enum {
+    OMPRT_OK = 0,
+    OMPRT_ERR_INVALID = 1,      /* bad argument; nothing launched */
+    OMPRT_ERR_NOMEM = 2,        /* device allocation failed (init / batch create) */
+    OMPRT_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    OMPRT_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+    OMPRT_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement */
+    OMPRT_ERR_NOT_INIT = 6,     /* NULL context */
+    OMPRT_ERR_DEVICE = 7        /* the sticky device status word is non-zero */
+} omprt_status;
+
+/* Device status bits (sticky, OR-ed by kernels, read by omprt_sync_status). */
+#define OMPRT_DEV_STACK_NOMEM 0x1u  /* shared stack and its pool were exhausted */
+#define OMPRT_DEV_STACK_ORDER 0x2u  /* free of a block that is not on top */
+#define OMPRT_DEV_TIMEOUT 0x4u      /* a bounded wait gave up */
+#define OMPRT_DEV_BAD_ARG 0x8u      /* a kernel saw an argument it cannot honour */
+
+/* Loop schedules (OpenMP loop-schedule semantics; the paper puts the
+ * division of loop iterations in the runtime, Sec. 1 and Sec. 2). */
+typedef enum {
+    OMPRT_SCHED_STATIC = 0,         /* chunk 0: one contiguous piece per thread;
+                                       chunk c > 0: same as STATIC_CHUNKED */
+    OMPRT_SCHED_STATIC_CHUNKED = 1, /* chunks of c, round robin over threads */
+    OMPRT_SCHED_DYNAMIC = 2,        /* chunks of c claimed at run time from a
+                                       per-team counter in global memory */
+    OMPRT_SCHED_AUTO = 3,           /* mapping left to the runtime: grid-stride
+                                       over 32-byte vectors */
+    OMPRT_SCHED_LEARNED = 4         /* schedule, chunk and teams chosen by the
+                                       context's cost model (see
+                                       omprt_set_cost_model), else the heuristic */
+} omprt_sched;
+
+typedef enum {
+    OMPRT_I32 = 0, OMPRT_U32 = 1, OMPRT_I64 = 2, OMPRT_U64 = 3,
+    OMPRT_F32 = 4, OMPRT_BF16 = 5, OMPRT_F64 = 6
+} omprt_dtype;
+
+typedef enum { OMPRT_OP_SUM = 0, OMPRT_OP_MAX = 1, OMPRT_OP_MIN = 2 } omprt_op;
+
+/* Accumulation precision of floating-point sums. */
+typedef enum {
+    OMPRT_PREC_COMP_F64 = 0,  /* compensated fp32 per thread and per team,
+                                 cross-team combine in fp64 (default) */
+    OMPRT_PREC_COMP_F32 = 1,  /* compensated fp32 throughout, fp32 combine */
+    OMPRT_PREC_NAIVE_F32 = 2  /* plain fp32 adds throughout */
+} omprt_precision;
+
+/* Loop bodies the executors run for each logical iteration i in [0, n). */
+typedef enum {
+    OMPRT_BODY_MAP_RECORD = 0, /* out: int32[n] owner id g*T + t;
+                                  y: int32[n] execution counters, incremented
+                                     atomically (NULL: skipped);
+                                  x: int32[G*T] per-thread "last" flags
+                                     (NULL: skipped) */
+    OMPRT_BODY_AXPY = 1,       /* y[i] = alpha*x[i] + y[i]; data_type F32
+                                  (single fma) or I32 (wrapping); reduces the
+                                  new y[i] */
+    OMPRT_BODY_STENCIL1D3 = 2, /* F32, out of place x -> out; interior
+                                  out[i] = fma(c1, x[i-1]+x[i+1], c0*x[i]),
+                                  end points copied; reduces out[i] */
+    OMPRT_BODY_STENCIL2D5 = 3, /* F32 ny x nx row major, x -> out; interior
+                                  out = fma(c1, (N+S)+(E+W), c0*C),
+                                  boundary copied; n must equal nx*ny */
+    OMPRT_BODY_DOT = 4,        /* F32, value x[i]*y[i] (rounded fp32 product)
+                                  fed to the reduction; writes nothing */
+    OMPRT_BODY_NONE = 5        /* value x[i] of data_type fed to the reduction */
+} omprt_body;
+
+/*
+ * A worksharing loop  for (v = lb; incr > 0 ? v <= ub : v >= ub; v += incr).
+ * Its trip count n is computed in the loop variable's type idx_type
+ * (I32/U32/I64/U64; bounds given as 64-bit patterns and checked to lie in the
+ * type; incr != 0).  Logical iteration i (v = lb + i*incr) touches element i
+ * of the data arrays.  Data arrays are device pointers; 32-byte alignment
+ * enables the 256-bit vector path, any 4-byte alignment is correct.
+ */
+typedef struct {
+    int64_t lb, ub, incr;
+    int32_t idx_type;          /* omprt_dtype, integer types only */
+    int32_t body;              /* omprt_body */
+    int32_t data_type;         /* omprt_dtype of x / y / out elements */
+    int32_t reserved;          /* must be 0 */
+    void *x, *y, *out;         /* device pointers, meaning per body */
+    double alpha;              /* AXPY scale (rounded to fp32 or int32) */
+    double c0, c1;             /* stencil weights (rounded to fp32) */
+    int64_t nx, ny;            /* STENCIL2D5 grid */
+} omprt_loop_desc;
+
+/* reduction(op: var) clause of a region.  result_dev: 8 bytes of device
+ * memory receiving a double (floating data) or an int64 (integer data);
+ * sums of int32 data are widened to int64 and wrap modulo 2^64. */
+typedef struct {
+    int32_t op;                /* omprt_op */
+    int32_t precision;         /* omprt_precision (floating sums only) */
+    void *result_dev;
+} omprt_reduce_desc;
+
+typedef struct omprt_ctx omprt_ctx;
+
+/* Create a context on a CUDA device: allocates the status word, the slot
+ * ring (partials, tickets, dispatch counters) and the stack fallback pool.
+ * All scratch starts zeroed and is left zeroed by every kernel, so no launch
+ * needs a memset (explicit initialisation of uninitialised team state,
+ * Sec. 3.1, "loader_uninitialized").  Returns OMPRT_ERR_CUDA / _NOMEM on
+ * failure with *ctx untouched. */
+omprt_status omprt_init(int device, omprt_ctx **ctx);
+
+/* Free the context's scratch.  The caller must have synchronised its streams. */
+omprt_status omprt_finalize(omprt_ctx *ctx);
+
+/* Reserve the per-team shared-memory stack capacity S for later launches
+ * (__kmpc_alloc_shared, Sec. 2.1, Listing 1).  S is rounded up to 16 and must
+ * not exceed 200 KiB.  The runtime's own per-launch temporaries (reduction
+ * scratch) are taken from this stack, so S below 1 KiB sends them to the
+ * global fallback pool.  Default after init: 4 KiB. */
+omprt_status omprt_alloc_shared(omprt_ctx *ctx, size_t bytes_per_team);
+
+/*
+ * Run one "target teams distribute parallel for" region:
+ *   level 1: the n logical iterations are split among num_teams teams in
+ *            contiguous balanced blocks (the first n % G blocks one longer);
+ *   level 2: each team's block is split among its thread_limit threads by
+ *            `sched` with chunk `chunk` (chunk numbering restarts at the
+ *            block start); AUTO ignores both levels and maps 32-byte vectors
+ *            grid-stride.
+ * num_teams: 1..2^31-1 (<= OMPRT_MAX_RED_TEAMS with a reduction or DYNAMIC),
+ *            0 = runtime choice; thread_limit: multiple of 32 in [32, 1024],
+ *            0 = 256; chunk >= 1 for STATIC_CHUNKED / DYNAMIC, 0 for STATIC
+ *            without chunk.  red may be NULL (no reduction clause).
+ * A reduction is finished inside the same launch: each team writes a partial,
+ * fences (the flush of Sec. 3.1, Listing 2) and takes a ticket with atomic
+ * inc (Sec. 3.1); the team drawing the last ticket combines all partials in
+ * team order and writes red->result_dev.  The ticket wraps to 0 by itself.
+ */
+omprt_status omprt_launch_region(omprt_ctx *ctx, const omprt_loop_desc *desc, int32_t sched,
+                                 int64_t chunk, int32_t num_teams, int32_t thread_limit,
+                                 const omprt_reduce_desc *red, void *stream);
+
+/* reduction(op) over n elements of dtype (F32, BF16, I32, I64) at data_dev:
+ * omprt_launch_region with BODY_NONE and schedule AUTO.  result_dev: 8 bytes
+ * (double for F32/BF16, int64 for integers).  precision: omprt_precision. */
+omprt_status omprt_reduce(omprt_ctx *ctx, int32_t op, int32_t dtype, int32_t precision,
+                          const void *data_dev, int64_t n, void *result_dev,
+                          int32_t num_teams, int32_t thread_limit, void *stream);
+
+/* Write, from device code, the static worksharing tuple that every thread of
+ * a composite launch would get (the __kmpc_for_static_init role, Sec. 1,
+ * Sec. 2): table_dev is int64[G*T][8], row g*T+t = team LB, UB, stride, last,
+ * thread LB, UB, stride, last, in user index space (64-bit two's complement
+ * on the widened bounds; an empty piece has LB = one step past the block,
+ * UB = LB - incr).  chunk 0 = no chunk. */
+omprt_status omprt_static_init_table(omprt_ctx *ctx, const omprt_loop_desc *desc, int64_t chunk,
+                                     int32_t num_teams, int32_t thread_limit, int64_t *table_dev,
+                                     void *stream);
+
+/* Host-only: the trip count n of desc's loop (rule above: bounds compared in
+ * the loop variable's signedness, distance in unsigned 64-bit arithmetic).
+ * Returns OMPRT_ERR_INVALID for a bad type, bound or incr == 0 and
+ * OMPRT_ERR_UNSUPPORTED for 2^63 or more iterations.  Needs no device. */
+omprt_status omprt_loop_trip_count(const omprt_loop_desc *desc, uint64_t *n_host);
+
+/* Synchronise `stream`, then read and clear the sticky device status word.
+ * *bits_host (may be NULL) receives the OMPRT_DEV_* bits.  Returns
+ * OMPRT_ERR_DEVICE if any bit was set, OMPRT_ERR_CUDA if the sync failed. */
+omprt_status omprt_sync_status(omprt_ctx *ctx, void *stream, uint32_t *bits_host);
+
+/* Static description of a status code. */
+const char *omprt_status_str(omprt_status s);
+
+/* Number of SMs of the context's device (0 for a NULL context). */
+int32_t omprt_sm_count(const omprt_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* Batched regions: many small target regions in one persistent kernel */
+/* ------------------------------------------------------------------ */
+/* The host calls omprt_batch_create once (it copies the region table to the
+ * device and sizes the work queue); omprt_launch_batch then runs every region
+ * in one persistent kernel whose CTAs claim (region, chunk) work items with
+ * an atomic add on a queue head (the paper's atomic add, Sec. 3.1).  Regions
+ * with a reduction combine their chunk partials in chunk order in the CTA
+ * that finishes the region's last chunk (ticket by atomic add).  The queue
+ * head and the tickets are reset by the last CTA to leave, so the launch can
+ * be replayed from a CUDA graph without a memset.
+ * Supported bodies: AXPY (F32), DOT (F32, needs red), STENCIL1D3 (F32);
+ * sched of each region must be AUTO; desc[i].lb = 0, incr = 1 (n = ub + 1).
+ * chunk_elems: elements per work item (multiple of 256, or 0 = 8192).
+ * reds may be NULL; reds[i].result_dev NULL means no reduction for region i. */
+typedef struct omprt_batch omprt_batch;
+omprt_status omprt_batch_create(omprt_ctx *ctx, const omprt_loop_desc *descs_host,
+                                const omprt_reduce_desc *reds_host, int32_t nregions,
+                                int64_t chunk_elems, omprt_batch **batch);
+/* num_ctas 0 = SMs x resident CTAs per SM; threads: multiple of 32 in
+ * [64, 1024], 0 = 256. */
+omprt_status omprt_launch_batch(omprt_batch *batch, int32_t num_ctas, int32_t threads,
+                                void *stream);
+omprt_status omprt_batch_destroy(omprt_batch *batch);
+/* Number of work items (chunks) in the batch; 0 for NULL. */
+int64_t omprt_batch_items(const omprt_batch *batch);
+
+/* ------------------------------------------------------------------ */
+/* Runtime self-tests run on the device (atomics, barrier, stack)      */
+/* ------------------------------------------------------------------ */
+/* Atomics of Sec. 3.1 (add, inc, max, exchange, cas) on one 32-bit word per
+ * op: num_teams x thread_limit threads each apply the op `reps` times.
+ *   words_dev: uint32[5] initial values in, final values out
+ *              [0] add 1, [1] inc with bound e, [2] max of the global thread
+ *              id, [3] exchange with the global thread id, [4] cas(expected =
+ *              thread id, desired = thread id + 1);
+ *   returned_dev: uint32[G*T*reps] the values the inc op returned (may be
+ *              NULL). */
+omprt_status omprt_test_atomics(omprt_ctx *ctx, int32_t num_teams, int32_t thread_limit,
+                                int32_t reps, uint32_t e, uint32_t *words_dev,
+                                uint32_t *returned_dev, void *stream);
+
+/* Team barrier check (Sec. 3.2, synchronisation): for `rounds` rounds each
+ * thread writes the round number to its shared slot, waits at the barrier,
+ * checks every slot, waits again.  sub_threads (multiple of 32, dividing
+ * thread_limit, or 0) also runs the same test with named barriers over
+ * sub-teams of that size.  errors_dev: uint32[1], += mismatches seen. */
+omprt_status omprt_test_barrier(omprt_ctx *ctx, int32_t num_teams, int32_t thread_limit,
+                                int32_t sub_threads, int32_t rounds, uint32_t *errors_dev,
+                                void *stream);
+
+/* Replay an alloc/free trace through the team shared-memory stack of every
+ * team (__kmpc_alloc_shared, Sec. 2.1, Listing 1).  ops_dev: int64[nops][2]
+ * (kind, arg): kind 0 = alloc(arg bytes), kind 1 = free of the block that
+ * op number arg (an earlier alloc) returned.  out_dev: int64[num_teams][nops][2]: alloc -> (region 0 shared /
+ * 1 pool / 2 failed, byte offset from that region's base), free -> (status
+ * bits raised, 0).  stack_bytes: S for this test (<= 200 KiB);
+ * pool_bytes: fallback bytes per team (<= OMPRT_POOL_BYTES_PER_TEAM).
+ * status_dev: int64[num_teams] OR of the bits per team.  nops <= 4096. */
+omprt_status omprt_test_stack(omprt_ctx *ctx, int32_t num_teams, int64_t stack_bytes,
+                              int64_t pool_bytes, const int64_t *ops_dev, int64_t nops,
+                              int64_t *out_dev, int64_t *status_dev, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Learned schedule: MLP cost model 16 -> 64 -> 64 -> 12 (fp32)        */
+/* ------------------------------------------------------------------ */
+/* Parameter vector layout (float32, 6028 values): W1[64][16], b1[64],
+ * W2[64][64], b2[64], W3[12][64], b3[12], row-major W[out][in].
+ * h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3. */
+#define OMPRT_MLP_IN 16
+#define OMPRT_MLP_HID 64
+#define OMPRT_MLP_OUT 12
+#define OMPRT_MLP_NPARAM 6028
+
+/* y_dev[B][12] = model(x_dev[B][16]). */
+omprt_status omprt_mlp_forward(omprt_ctx *ctx, const float *params_dev, const float *x_dev,
+                               int32_t batch, float *y_dev, void *stream);
+/* Mean-squared-error loss over the batch and the 12 outputs and its gradient:
+ * grad_dev[6028] = d loss / d params (overwritten), loss_dev[1] (may be NULL). */
+omprt_status omprt_mlp_loss_grad(omprt_ctx *ctx, const float *params_dev, const float *x_dev,
+                                 const float *target_dev, int32_t batch, float *grad_dev,
+                                 float *loss_dev, void *stream);
+/* One bias-corrected Adam step (Kingma & Ba 2015) at step number t >= 1 on
+ * params_dev, with moment buffers m_dev, v_dev (zero before step 1). */
+omprt_status omprt_mlp_adam(omprt_ctx *ctx, float *params_dev, const float *grad_dev,
+                            float *m_dev, float *v_dev, int32_t n, int32_t t, float lr,
+                            float beta1, float beta2, float eps, void *stream);
+
+/* Learned-schedule configuration table: index k in [0, 12) of the model's
+ * output is configuration k: sched_host[k], chunk_host[k], teams_per_sm_host[k]
+ * (num_teams = teams_per_sm * SMs) and threads_host[k]; any pointer may be NULL. */
+omprt_status omprt_learned_configs(int32_t *sched_host, int64_t *chunk_host,
+                                   int32_t *teams_per_sm_host, int32_t *threads_host);
+
+/* Install (params_host != NULL) or remove (NULL) the cost model used by
+ * OMPRT_SCHED_LEARNED, with the feature standardisation (mean_host[16],
+ * std_host[16]).  The model is copied; inference runs on the host at launch
+ * time, takes the argmin of the 12 predicted log-times, and falls back to the
+ * heuristic when no model is installed or an output is not finite. */
+omprt_status omprt_set_cost_model(omprt_ctx *ctx, const float *params_host,
+                                  const float *mean_host, const float *std_host);
+
+/* Features (16 floats) the cost model sees for a loop, and the configuration
+ * index the installed model (or, without one, the heuristic) picks. */
+omprt_status omprt_loop_features(const omprt_ctx *ctx, const omprt_loop_desc *desc,
+                                 int32_t has_reduction, float *features_host);
+omprt_status omprt_choose_config(const omprt_ctx *ctx, const omprt_loop_desc *desc,
+                                 int32_t has_reduction, int32_t *config_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OMPRT_H_ */

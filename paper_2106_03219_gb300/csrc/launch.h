@@ -1,0 +1,40 @@
+// Host-side entry points of the executor translation units (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "region.cuh"
+
+namespace rt {
+
+// Reduction accumulator selected for a launch.
+enum AccKind : int {
+  kAccNone = 0,
+  kAccSumI64,
+  kAccCompF32,
+  kAccNaiveF32,
+  kAccMaxF32,
+  kAccMinF32,
+  kAccMaxI64,
+  kAccMinI64,
+};
+
+// Launch one region kernel instance.  Returns cudaErrorNotSupported for a
+// (body, data type, accumulator) combination that has no instance.
+cudaError_t launch_region_f32(int body, int dtype, int acc, int sched, unsigned grid,
+                              unsigned block, size_t smem, cudaStream_t st, const RegionArgs& a);
+cudaError_t launch_region_int(int body, int dtype, int acc, int sched, unsigned grid,
+                              unsigned block, size_t smem, cudaStream_t st, const RegionArgs& a);
+
+// Support kernels (k_support.cu).
+cudaError_t launch_static_table(uint64_t n, int64_t lb, int64_t incr, uint64_t chunk, unsigned G,
+                                unsigned T, int64_t* table, cudaStream_t st);
+cudaError_t launch_test_atomics(unsigned G, unsigned T, int reps, uint32_t e, uint32_t* words,
+                                uint32_t* returned, uint32_t* status, cudaStream_t st);
+cudaError_t launch_test_barrier(unsigned G, unsigned T, unsigned sub, int rounds, uint32_t* errors,
+                                cudaStream_t st);
+cudaError_t launch_test_stack(unsigned G, uint32_t S, uint32_t Q, unsigned char* pool,
+                              const int64_t* ops, int64_t nops, int64_t* out, int64_t* status_out,
+                              uint32_t* status, cudaStream_t st);
+
+}  // namespace rt

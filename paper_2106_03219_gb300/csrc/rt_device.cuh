@@ -1,0 +1,391 @@
+// Device runtime core for sm_103a: thread hierarchy, atomics, barriers, the
+// static iteration split, the team shared-memory stack, accumulators and the
+// team / cross-team reduction.  Header-only, instantiated into each executor
+// kernel (the role the paper gives to linking the runtime as bitcode into every
+// kernel so it is specialised with it, Sec. 2.3).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "omprt.h"
+
+namespace rt {
+
+// ---------------------------------------------------------------------------
+// Thread hierarchy: one OpenMP team is one thread block (Sec. 3.1, "Global
+// Shared Variables"); ids come from the hardware registers (Sec. 3.2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t team_id() { return blockIdx.x; }
+__device__ __forceinline__ uint32_t num_teams() { return gridDim.x; }
+__device__ __forceinline__ uint32_t thread_id() { return threadIdx.x; }
+__device__ __forceinline__ uint32_t team_size() { return blockDim.x; }
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t warp_id() { return threadIdx.x >> 5; }
+
+// ---------------------------------------------------------------------------
+// The five runtime atomics (Sec. 3.1, Listing 3 and the inc definition after
+// it), sequentially consistent on 32-bit words at device scope: a full fence
+// on both sides of the hardware read-modify-write.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t atomic_add(uint32_t* x, uint32_t e) {
+  __threadfence();
+  uint32_t v = atomicAdd(x, e);
+  __threadfence();
+  return v;
+}
+// { v = x; x = x >= e ? 0 : x + 1; } -- exactly the hardware atom.inc rule.
+__device__ __forceinline__ uint32_t atomic_inc(uint32_t* x, uint32_t e) {
+  __threadfence();
+  uint32_t v = atomicInc(x, e);
+  __threadfence();
+  return v;
+}
+// { v = x; if (x < e) x = e; }
+__device__ __forceinline__ uint32_t atomic_max(uint32_t* x, uint32_t e) {
+  __threadfence();
+  uint32_t v = atomicMax(x, e);
+  __threadfence();
+  return v;
+}
+__device__ __forceinline__ uint32_t atomic_exchange(uint32_t* x, uint32_t e) {
+  __threadfence();
+  uint32_t v = atomicExch(x, e);
+  __threadfence();
+  return v;
+}
+// { v = x; if (x == e) x = d; }
+__device__ __forceinline__ uint32_t atomic_cas(uint32_t* x, uint32_t e, uint32_t d) {
+  __threadfence();
+  uint32_t v = atomicCAS(x, e, d);
+  __threadfence();
+  return v;
+}
+// __kmpc_flush (Sec. 3.1, Listing 2): a device-scope fence.
+__device__ __forceinline__ void flush() { __threadfence(); }
+
+__device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {
+  atomicOr(status, bits);
+}
+
+// ---------------------------------------------------------------------------
+// Synchronisation (Sec. 3.2): the whole team, or a named sub-team barrier
+// over `count` threads (a multiple of 32) on hardware barrier `id` (1..15).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void team_barrier() { __syncthreads(); }
+__device__ __forceinline__ void named_barrier(uint32_t id, uint32_t count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Static split without chunk: entity k of P gets q + (k < r) iterations
+// starting at k*q + min(k, r), q = n / P, r = n % P (balanced blocks in
+// entity order).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_even(uint64_t n, uint32_t P, uint32_t k, uint64_t& start,
+                                           uint64_t& count) {
+  const uint64_t q = n / P;
+  const uint32_t r = (uint32_t)(n - q * P);
+  count = q + (k < r ? 1u : 0u);
+  start = q * k + (k < r ? k : r);
+}
+
+// ---------------------------------------------------------------------------
+// Team shared-memory stack (__kmpc_alloc_shared, Sec. 2.1, Listing 1).
+// LIFO in the team's dynamic shared memory (S bytes), overflow to this team's
+// slice of a global pool (also LIFO), then NULL plus a status bit.  Requests
+// are rounded up to 16 bytes (0 counts as 1).  The state is a team-shared
+// variable that starts uninitialised and is set explicitly at kernel entry
+// (Sec. 3.1, "loader_uninitialized").  Calls are made by one thread of the
+// team (the runtime serialises through thread 0).
+// ---------------------------------------------------------------------------
+struct TeamStack {
+  uint32_t top_s, cap_s, top_q, cap_q;
+  unsigned char* pool;
+};
+
+extern __shared__ __align__(16) unsigned char rt_dyn_smem[];
+static __shared__ TeamStack rt_stack;
+static __shared__ void* rt_bcast_ptr;
+static __shared__ int rt_bcast_flag;
+
+__device__ __forceinline__ void stack_init(uint32_t cap_s, unsigned char* pool, uint32_t cap_q) {
+  rt_stack.top_s = 0;
+  rt_stack.cap_s = cap_s;
+  rt_stack.top_q = 0;
+  rt_stack.cap_q = pool ? cap_q : 0;
+  rt_stack.pool = pool;
+}
+
+__device__ __forceinline__ uint64_t stack_round(uint64_t bytes) {
+  return ((bytes ? bytes : 1) + 15) & ~uint64_t(15);
+}
+
+__device__ inline void* alloc_shared(uint64_t bytes, uint32_t* status) {
+  const uint64_t r = stack_round(bytes);
+  TeamStack& s = rt_stack;
+  if (r <= (uint64_t)(s.cap_s - s.top_s)) {
+    void* p = rt_dyn_smem + s.top_s;
+    s.top_s += (uint32_t)r;
+    return p;
+  }
+  if (r <= (uint64_t)(s.cap_q - s.top_q)) {
+    void* p = s.pool + s.top_q;
+    s.top_q += (uint32_t)r;
+    return p;
+  }
+  set_status(status, OMPRT_DEV_STACK_NOMEM);
+  return nullptr;
+}
+
+// Region of a pointer returned by alloc_shared: 0 shared, 1 pool, 2 neither.
+__device__ __forceinline__ int stack_region(const void* p) {
+  const unsigned char* c = (const unsigned char*)p;
+  if (c >= rt_dyn_smem && c < rt_dyn_smem + rt_stack.cap_s) return 0;
+  if (rt_stack.pool && c >= rt_stack.pool && c < rt_stack.pool + rt_stack.cap_q) return 1;
+  return 2;
+}
+
+// Returns the status bits raised (0 or OMPRT_DEV_STACK_ORDER).
+__device__ inline uint32_t free_shared(void* p, uint64_t bytes, uint32_t* status) {
+  if (p == nullptr) return 0;
+  const uint64_t r = stack_round(bytes);
+  TeamStack& s = rt_stack;
+  const unsigned char* c = (const unsigned char*)p;
+  const int reg = stack_region(p);
+  if (reg == 0 && c + r == rt_dyn_smem + s.top_s) {
+    s.top_s -= (uint32_t)r;
+    return 0;
+  }
+  if (reg == 1 && c + r == s.pool + s.top_q) {
+    s.top_q -= (uint32_t)r;
+    return 0;
+  }
+  set_status(status, OMPRT_DEV_STACK_ORDER);
+  return OMPRT_DEV_STACK_ORDER;
+}
+
+// Team-wide temporary: thread 0 allocates, every thread gets the pointer.
+// Must be reached by the whole team.
+__device__ inline void* team_alloc(uint64_t bytes, uint32_t* status) {
+  if (threadIdx.x == 0) rt_bcast_ptr = alloc_shared(bytes, status);
+  team_barrier();
+  void* p = rt_bcast_ptr;
+  team_barrier();
+  return p;
+}
+__device__ inline void team_free(void* p, uint64_t bytes, uint32_t* status) {
+  team_barrier();
+  if (threadIdx.x == 0) free_shared(p, bytes, status);
+}
+
+// ---------------------------------------------------------------------------
+// Global-memory access helpers (inline PTX; 256-bit vectors need sm_100+).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ld_nc(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_f(const float* p) {
+  float v;
+  asm("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_nc(const int32_t* p) {
+  int32_t v;
+  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_i(const int32_t* p) {
+  int32_t v;
+  asm("ld.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int64_t ld_nc(const int64_t* p) {
+  int64_t v;
+  asm("ld.global.nc.L1::no_allocate.s64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint16_t ld_nc(const uint16_t* p) {
+  uint16_t v;
+  asm("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return v;
+}
+
+// 32 bytes = 8 x 32-bit
+__device__ __forceinline__ void ld8_nc(const void* p, uint32_t (&r)[8]) {
+  asm("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "l"(p));
+}
+__device__ __forceinline__ void ld8(const void* p, uint32_t (&r)[8]) {
+  asm("ld.global.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "l"(p));
+}
+__device__ __forceinline__ void st8(void* p, const uint32_t (&r)[8]) {
+  asm volatile("st.global.L1::no_allocate.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+               "r"(r[7])
+               : "memory");
+}
+// 32 bytes = 4 x 64-bit
+__device__ __forceinline__ void ld4x64_nc(const void* p, uint64_t (&r)[4]) {
+  asm("ld.global.nc.L1::no_allocate.v4.b64 {%0,%1,%2,%3}, [%4];"
+      : "=l"(r[0]), "=l"(r[1]), "=l"(r[2]), "=l"(r[3])
+      : "l"(p));
+}
+
+__device__ __forceinline__ float as_f(uint32_t u) { return __uint_as_float(u); }
+__device__ __forceinline__ uint32_t as_u(float f) { return __float_as_uint(f); }
+
+// ---------------------------------------------------------------------------
+// Accumulators (thread-local partial of a reduction clause).
+// Each provides: Part (the value carried through the team tree), part(),
+// merge(Part, Part), identity(), shfl_xor(Part, mask).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  // Knuth's TwoSum: s + e == a + b exactly, for any magnitudes.
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+struct AccNone {
+  static constexpr bool kActive = false;
+  template <class V>
+  __device__ __forceinline__ void add(V) {}
+};
+
+// Integer sums, exact modulo 2^64.
+struct AccSumI64 {
+  static constexpr bool kActive = true;
+  using Part = unsigned long long;
+  Part s = 0;
+  __device__ __forceinline__ void add(int32_t v) { s += (Part)(int64_t)v; }
+  __device__ __forceinline__ void add(int64_t v) { s += (Part)v; }
+  __device__ __forceinline__ Part part() const { return s; }
+  __device__ static __forceinline__ Part identity() { return 0; }
+  __device__ static __forceinline__ Part merge(Part a, Part b) { return a + b; }
+  __device__ static __forceinline__ Part shfl(Part a, int m) {
+    return __shfl_xor_sync(0xffffffffu, a, m);
+  }
+};
+
+template <bool kMax>
+struct AccExtI64 {
+  static constexpr bool kActive = true;
+  using Part = long long;
+  Part m = kMax ? (Part)INT64_MIN : (Part)INT64_MAX;
+  __device__ __forceinline__ void add(int32_t v) { add((int64_t)v); }
+  __device__ __forceinline__ void add(int64_t v) { m = kMax ? (v > m ? v : m) : (v < m ? v : m); }
+  __device__ __forceinline__ Part part() const { return m; }
+  __device__ static __forceinline__ Part identity() {
+    return kMax ? (Part)INT64_MIN : (Part)INT64_MAX;
+  }
+  __device__ static __forceinline__ Part merge(Part a, Part b) {
+    return kMax ? (a > b ? a : b) : (a < b ? a : b);
+  }
+  __device__ static __forceinline__ Part shfl(Part a, int mm) {
+    return __shfl_xor_sync(0xffffffffu, a, mm);
+  }
+};
+
+// Compensated fp32 sum: running (s, c) with s + c the sum so far; every add
+// is an exact TwoSum whose rounding error is collected in c.
+struct AccCompF32 {
+  static constexpr bool kActive = true;
+  using Part = float2;  // (s, c)
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float t, e;
+    two_sum(s, v, t, e);
+    s = t;
+    c = __fadd_rn(c, e);
+  }
+  __device__ __forceinline__ Part part() const { return make_float2(s, c); }
+  __device__ static __forceinline__ Part identity() { return make_float2(0.f, 0.f); }
+  __device__ static __forceinline__ Part merge(Part a, Part b) {
+    float t, e;
+    two_sum(a.x, b.x, t, e);
+    return make_float2(t, __fadd_rn(__fadd_rn(a.y, b.y), e));
+  }
+  __device__ static __forceinline__ Part shfl(Part a, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
+  }
+};
+
+struct AccNaiveF32 {
+  static constexpr bool kActive = true;
+  using Part = float;
+  float s = 0.f;
+  __device__ __forceinline__ void add(float v) { s = __fadd_rn(s, v); }
+  __device__ __forceinline__ Part part() const { return s; }
+  __device__ static __forceinline__ Part identity() { return 0.f; }
+  __device__ static __forceinline__ Part merge(Part a, Part b) { return __fadd_rn(a, b); }
+  __device__ static __forceinline__ Part shfl(Part a, int m) {
+    return __shfl_xor_sync(0xffffffffu, a, m);
+  }
+};
+
+// max / min over fp32; a NaN operand is skipped (fmaxf / fminf rule).
+template <bool kMax>
+struct AccExtF32 {
+  static constexpr bool kActive = true;
+  using Part = float;
+  float m = kMax ? -__builtin_huge_valf() : __builtin_huge_valf();
+  __device__ __forceinline__ void add(float v) { m = kMax ? fmaxf(m, v) : fminf(m, v); }
+  __device__ __forceinline__ Part part() const { return m; }
+  __device__ static __forceinline__ Part identity() {
+    return kMax ? -__builtin_huge_valf() : __builtin_huge_valf();
+  }
+  __device__ static __forceinline__ Part merge(Part a, Part b) {
+    return kMax ? fmaxf(a, b) : fminf(a, b);
+  }
+  __device__ static __forceinline__ Part shfl(Part a, int mm) {
+    return __shfl_xor_sync(0xffffffffu, a, mm);
+  }
+};
+
+// fp64 sum used only for the cross-team combine (the one step kept in fp64).
+struct CombF64 {
+  using Part = double;
+  __device__ static __forceinline__ Part identity() { return 0.0; }
+  __device__ static __forceinline__ Part merge(Part a, Part b) { return __dadd_rn(a, b); }
+  __device__ static __forceinline__ Part shfl(Part a, int m) {
+    return __shfl_xor_sync(0xffffffffu, a, m);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Team reduction: butterfly over the warp (shuffle xor), then the per-warp
+// values through shared scratch (>= 32 Parts) and one more warp butterfly.
+// The tree shape depends only on the team size, so the result is the same on
+// every run.  Returns the team value in every thread of warp 0.
+// ---------------------------------------------------------------------------
+template <class M>
+__device__ __forceinline__ typename M::Part warp_reduce(typename M::Part v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = M::merge(v, M::shfl(v, m));
+  return v;
+}
+
+template <class M>
+__device__ inline typename M::Part team_reduce(typename M::Part v, typename M::Part* scratch) {
+  v = warp_reduce<M>(v);
+  const uint32_t nw = blockDim.x >> 5;
+  if (lane_id() == 0) scratch[warp_id()] = v;
+  team_barrier();
+  if (warp_id() == 0) {
+    v = lane_id() < nw ? scratch[lane_id()] : M::identity();
+    v = warp_reduce<M>(v);
+  }
+  team_barrier();
+  return v;
+}
+
+}  // namespace rt

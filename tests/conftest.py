@@ -26,3 +26,17 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def rt():
+    """One runtime context on cuda:0 for the GPU tests (built on first use)."""
+    import torch
+    from paper_2106_03219_gb300 import build_lib
+    from paper_2106_03219_gb300 import omprt as R
+    build_lib.build()
+    torch.cuda.init()
+    r = R.Runtime(0)
+    yield r
+    torch.cuda.synchronize()
+    r.close()

@@ -1,0 +1,89 @@
+"""GPU parity: worksharing maps (static tables and owner maps bit-exact
+against the oracle; dynamic and auto schedules by invariants)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2106_03219_gb300 import omprt as R
+from gpu_helpers import dev, host
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = [("i64", 0, 1), ("i32", -5, 3), ("i64", 100, -7), ("u32", 4000000000, -2),
+          ("u64", (1 << 64) - 60000, 1), ("i32", (1 << 31) - 200000, 1)]
+
+
+@pytest.mark.parametrize("t,lb,incr", BOUNDS)
+def test_static_init_table_bit_exact(rt, t, lb, incr):
+    import torch
+    for n in (0, 1, 5, 17, 1000, 123457):
+        if t in ("u64", "i32") and n * abs(incr) > 190000:
+            continue
+        ub = lb + (n - 1) * incr if n else lb - incr
+        desc = R.loop_desc(R.BODY_NONE, lb=lb, ub=ub, incr=incr, idx_type=R.TYPE_CODES[t],
+                           data_type=R.F32)
+        for G, T in ((1, 1), (3, 32), (7, 96), (152, 1024)):
+            for c in (0, 1, 3, 8, 64):
+                tab = torch.empty((G * T, 8), dtype=torch.int64, device="cuda")
+                rt.static_init_table(desc, c, G, T, tab)
+                ref = O.composite_table(lb, ub, incr, t, G, T, c)
+                assert np.array_equal(host(tab), ref), (n, G, T, c)
+
+
+def _map_record(rt, n, G, T, sched, chunk):
+    import torch
+    owner = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
+    count = torch.zeros((max(n, 1),), dtype=torch.int32, device="cuda")
+    last = torch.full((G * T,), -1, dtype=torch.int32, device="cuda")
+    desc = R.loop_desc(R.BODY_MAP_RECORD, n=n, x=last, y=count, out=owner, data_type=R.I32)
+    rt.launch_region(desc, sched, chunk, G, T)
+    assert rt.sync_status() == 0
+    return host(owner)[:n], host(count)[:n], host(last)
+
+
+CASES = [(0, 4, 32), (1, 1, 32), (31, 4, 32), (1000, 13, 128), (100003, 148, 256),
+         ((1 << 20) + 7, 1184, 1024), (5000, 3, 1024)]
+
+
+@pytest.mark.parametrize("n,G,T", CASES)
+@pytest.mark.parametrize("chunk", [0, 1, 5, 8, 64])
+def test_static_owner_map_bit_exact(rt, n, G, T, chunk):
+    sched = R.SCHED_STATIC if chunk == 0 else R.SCHED_STATIC_CHUNKED
+    owner, count, last = _map_record(rt, n, G, T, sched, chunk)
+    assert np.array_equal(owner, O.owner_map(n, G, T, chunk))
+    assert np.all(count == 1)
+    assert int((last == 1).sum()) == (1 if n else 0)
+    if n:
+        assert last[owner[n - 1]] == 1
+
+
+@pytest.mark.parametrize("n,G,T", CASES)
+@pytest.mark.parametrize("chunk", [1, 7, 256])
+def test_dynamic_invariants(rt, n, G, T, chunk):
+    owner, count, last = _map_record(rt, n, G, T, R.SCHED_DYNAMIC, chunk)
+    assert np.all(count == 1)                         # every iteration exactly once
+    assert int((last == 1).sum()) == (1 if n else 0)  # exactly one thread is last
+    if n:
+        assert last[owner[n - 1]] == 1
+    for g in range(G):
+        bs, bn = O.static_nochunk(n, G, g)            # level 1 stays static
+        blk = owner[bs:bs + bn]
+        assert np.all(blk // T == g)                  # iterations stay in the team
+        idx = np.arange(bn)
+        same = (idx[1:] // chunk) == (idx[:-1] // chunk)   # neighbours in one chunk
+        assert np.all(blk[1:][same] == blk[:-1][same])      # each chunk has one owner
+
+
+@pytest.mark.parametrize("n,G,T", CASES)
+def test_auto_invariants(rt, n, G, T):
+    owner, count, last = _map_record(rt, n, G, T, R.SCHED_AUTO, 0)
+    assert np.all(count == 1)
+    assert np.all((owner >= 0) & (owner < G * T))
+    assert int((last == 1).sum()) == (1 if n else 0)
+
+
+def test_dynamic_counters_reset_between_launches(rt):
+    # a second launch on the same slots must see zeroed counters
+    for _ in range(2 * R.SLOTS + 3):
+        owner, count, last = _map_record(rt, 4099, 9, 64, R.SCHED_DYNAMIC, 16)
+        assert np.all(count == 1)
