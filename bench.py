@@ -1,0 +1,437 @@
+"""Benchmark: loop GB/s of the OpenMP device-runtime hot path on GB300.
+
+One step = one pass of the worksharing workload: fp32 axpy y = 3x + y over
+n = 2^26 and the 2-D 5-point stencil over a 4096 x 4096 fp32 grid, each run
+as a "teams distribute parallel for" region under the six schedules
+static(1), static(8), static(64), static (no chunk), dynamic(256) and auto,
+at the teams / threads the tuning table gives for that schedule.
+
+value     = algorithmic bytes of the step (12 B per axpy iteration, 8 B per
+            stencil point) / device time of the step (CUDA events).
+e2e       = the same bytes / time of a step through the C ABI with the inputs
+            copied in from pinned host memory and the results copied back.
+roofline  = the kernel with the largest share of the step: its algorithmic
+            bytes per launch / its mean launch time, against the measured HBM
+            copy bandwidth.
+cpu_baseline / --impl reference = the CPU oracle timed on a bounded sample.
+
+Launch: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference];
+for N > 1 under torch.distributed.run, every rank runs the same workload on
+its own GPU (weak scaling, no data-path collective; max time over ranks).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_AXPY = 1 << 26
+GRID = 4096
+AXPY_BYTES = 12 * N_AXPY
+STENCIL_BYTES = 8 * GRID * GRID
+METRIC = "loop GB/s vs HBM peak (worksharing sweep step: fp32 axpy 2^26 + 2D 5-point stencil 4096^2, 6 schedules)"
+UNIT = "GB/s"
+
+# (label, sched, chunk)
+SCHEDULES = [("static1", 1, 1), ("static8", 1, 8), ("static64", 1, 64), ("static", 0, 0),
+             ("dynamic256", 2, 256), ("auto", 3, 0)]
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2106_03219_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "omprt.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def tuned_points(sm_count):
+    """(teams, threads) per schedule label: the autotuner's table if one was
+    committed for this source, else 4 teams per SM x 256 threads."""
+    from paper_2106_03219_gb300 import autotune
+    table = autotune.load_sweep_table()
+    pts = {}
+    for label, _, _ in SCHEDULES:
+        for body in ("axpy", "stencil2d"):
+            key = "%s/%s" % (body, label)
+            if table and key in table:
+                pts[key] = tuple(table[key])
+            else:
+                pts[key] = (4 * sm_count, 256)
+    return pts
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        load = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value, ws):
+    """Largest value over all ranks (identity for one rank)."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# -- CPU oracle leg ----------------------------------------------------------------
+
+def oracle_sample_step(x, y, grid):
+    """One bounded sample of the step on the CPU oracle: axpy over x/y and the
+    stencil over grid, once per schedule (the oracle is sequential, so every
+    schedule runs the same loop).  Returns algorithmic bytes."""
+    import oracle as O
+    nbytes = 0
+    for _ in SCHEDULES:
+        O.axpy_f32(3.0, x, y)
+        O.stencil2d5(grid)
+        nbytes += 12 * x.size + 8 * grid.size
+    return nbytes
+
+
+def cpu_baseline(budget_s=10.0):
+    from paper_2106_03219_gb300 import inputs
+    n, g = 1 << 22, 1024
+    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+    grid = inputs.grid_f32(g, g, 0)
+    oracle_sample_step(x, y, grid)  # builds / loads the oracle
+    t0 = time.perf_counter()
+    nbytes, steps = 0, 0
+    while time.perf_counter() - t0 < budget_s:
+        nbytes += oracle_sample_step(x, y, grid)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d oracle steps of fp32 axpy n=2^22 + 2D stencil %dx%d x 6 schedules "
+                      "(single-threaded C), %.1f s" % (steps, g, g, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2106_03219_gb300 import inputs
+    n, g = 1 << 22, 1024
+    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+    grid = inputs.grid_f32(g, g, 0)
+    for _ in range(args.warmup):
+        oracle_sample_step(x, y, grid)
+    t0 = time.perf_counter()
+    nbytes = 0
+    for _ in range(args.steps):
+        nbytes += oracle_sample_step(x, y, grid)
+    dt = time.perf_counter() - t0
+    v = nbytes / dt / 1e9
+    sample = ("per step: fp32 axpy n=2^22 + 2D stencil %dx%d x 6 schedules on the CPU oracle "
+              "(single-threaded C)" % (g, g))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_dict(None),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(points):
+    c = {"workload": "worksharing sweep step: fp32 axpy y=3x+y n=2^26 and 2D 5-point stencil "
+                     "4096x4096 fp32 (uniform [0,1), seeds 0/1), each under schedules "
+                     "static(1), static(8), static(64), static, dynamic(256), auto",
+         "l2": "inputs larger than L2: every stencil launch follows an 805 MB axpy stream",
+         "parallelism": "one GPU per rank, independent copies (weak scaling)"}
+    if points:
+        c["teams_threads"] = {k: list(v) for k, v in points.items()}
+    return c
+
+
+# -- GPU leg ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--single", default=None,
+                    help="profiling aid: only launch plan entries whose name contains this "
+                         "(e.g. axpy/auto), warmup + steps times, and print their mean time")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2106_03219_gb300 import build_lib, inputs
+    from paper_2106_03219_gb300 import omprt as R
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build_lib.build()
+    rt = R.Runtime(local)
+    sms = rt.sm_count
+    points = tuned_points(sms)
+    stream = torch.cuda.current_stream()
+
+    x = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 0)).cuda()
+    y = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 1)).cuda()
+    grid = torch.from_numpy(inputs.grid_f32(GRID, GRID, 0)).cuda()
+    out = torch.empty_like(grid)
+
+    def launches(xx, yy, gg, oo):
+        L = []
+        for label, sched, chunk in SCHEDULES:
+            G, T = points["axpy/" + label]
+            L.append(("axpy/" + label, AXPY_BYTES,
+                      R.loop_desc(R.BODY_AXPY, n=N_AXPY, x=xx, y=yy, alpha=3.0), sched, chunk, G, T))
+            G, T = points["stencil2d/" + label]
+            L.append(("stencil2d/" + label, STENCIL_BYTES,
+                      R.loop_desc(R.BODY_STENCIL2D5, n=GRID * GRID, x=gg, out=oo, nx=GRID,
+                                  ny=GRID), sched, chunk, G, T))
+        return L
+
+    plan = launches(x, y, grid, out)
+    if args.single:
+        return run_single(rt, torch, plan, args)
+    step_bytes = sum(b for _, b, *_ in plan)
+
+    def run_step(record=None):
+        for i, (name, _, desc, sched, chunk, G, T) in enumerate(plan):
+            if record is not None:
+                record[i][0].record(stream)
+            rt.launch_region(desc, sched, chunk, G, T, stream=stream)
+            if record is not None:
+                record[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        run_step()
+    torch.cuda.synchronize()
+    assert rt.sync_status() == 0
+
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in plan] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        run_step(ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    ms_total = max_over_ranks(ms_total, ws)
+    ms_step = ms_total / args.steps
+    value = step_bytes * ws / (ms_step * 1e-3) / 1e9
+    assert rt.sync_status() == 0
+
+    # per-kernel mean launch times; the dominant kernel is the largest share
+    per = {}
+    for i, (name, nbytes, *_rest) in enumerate(plan):
+        ts = [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)]
+        per[name] = (nbytes, statistics.mean(ts))
+    dom = max(per, key=lambda k: per[k][1])
+    peak, peak_kind = measured_peaks()
+    achieved = per[dom][0] / (per[dom][1] * 1e-3) / 1e9
+    traffic = traffic_for(dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    kernels = {k: {"ms": v[1], "GBps": v[0] / (v[1] * 1e-3) / 1e9,
+                   "frac": v[0] / (v[1] * 1e-3) / 1e9 / peak} for k, v in per.items()}
+
+    # end to end through the C ABI with host buffers
+    e2e = measure_e2e(rt, R, torch, inputs, plan, points, args.e2e_steps, launches)
+    e2e_val = max_over_ranks(e2e["ms"], ws)
+    e2e_line = {"value": step_bytes * ws / (e2e_val * 1e-3) / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": config_dict(points),
+                "e2e": e2e_line, "roofline": roofline, "cpu_baseline": cpu,
+                "gpu_launches": len(plan) * args.steps, "clocks": clk,
+                "kernels": kernels, "source_hash": source_hash()}
+        print(json.dumps(line))
+    rt.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_single(rt, torch, plan, args):
+    sel = [p for p in plan if args.single in p[0]]
+    if not sel:
+        raise SystemExit("no plan entry matches %r" % args.single)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for name, _, desc, sched, chunk, G, T in sel:
+            rt.launch_region(desc, sched, chunk, G, T, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for name, _, desc, sched, chunk, G, T in sel:
+            rt.launch_region(desc, sched, chunk, G, T, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert rt.sync_status() == 0
+    ms = e0.elapsed_time(e1) / args.steps
+    nbytes = sum(p[1] for p in sel)
+    print(json.dumps({"single": [p[0] for p in sel], "ms": ms,
+                      "GBps": nbytes / (ms * 1e-3) / 1e9}))
+    rt.close()
+    return 0
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, if it
+    was taken on the current source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != source_hash():
+        return None
+    v = d.get("kernels", {}).get(kernel)
+    return None if v is None else float(v)
+
+
+def measure_e2e(rt, R, torch, inputs, plan, points, steps, launches):
+    """Step time with H2D of the inputs from pinned memory and D2H of the
+    results inside the timed region."""
+    hx = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 0)).pin_memory()
+    hy = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 1)).pin_memory()
+    hg = torch.from_numpy(inputs.grid_f32(GRID, GRID, 0)).pin_memory()
+    ry = torch.empty_like(hy).pin_memory()
+    ro = torch.empty_like(hg).pin_memory()
+    dx = torch.empty(N_AXPY, device="cuda")
+    dy = torch.empty(N_AXPY, device="cuda")
+    dg = torch.empty((GRID, GRID), device="cuda")
+    do = torch.empty_like(dg)
+    L = launches(dx, dy, dg, do)
+    stream = torch.cuda.current_stream()
+
+    def one():
+        dx.copy_(hx, non_blocking=True)
+        dy.copy_(hy, non_blocking=True)
+        dg.copy_(hg, non_blocking=True)
+        for name, _, desc, sched, chunk, G, T in L:
+            rt.launch_region(desc, sched, chunk, G, T, stream=stream)
+        ry.copy_(dy, non_blocking=True)
+        ro.copy_(do, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        one()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    h2d = (hx.numel() + hy.numel() + hg.numel()) * 4
+    d2h = (ry.numel() + ro.numel()) * 4
+    return {"ms": t0.elapsed_time(t1) / steps, "h2d": h2d, "d2h": d2h}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -301,7 +301,9 @@ omprt_status omprt_test_stack(omprt_ctx *ctx, int32_t num_teams, int64_t stack_b
 omprt_status omprt_mlp_forward(omprt_ctx *ctx, const float *params_dev, const float *x_dev,
                                int32_t batch, float *y_dev, void *stream);
 /* Mean-squared-error loss over the batch and the 12 outputs and its gradient:
- * grad_dev[6028] = d loss / d params (overwritten), loss_dev[1] (may be NULL). */
+ * grad_dev[6028] = d loss / d params (overwritten), loss_dev[1] (may be NULL).
+ * batch in [1, 16384]; the per-sample activations go to context scratch, so
+ * calls on one context must not overlap on the device. */
 omprt_status omprt_mlp_loss_grad(omprt_ctx *ctx, const float *params_dev, const float *x_dev,
                                  const float *target_dev, int32_t batch, float *grad_dev,
                                  float *loss_dev, void *stream);

@@ -183,6 +183,8 @@ omprt_status omprt_init(int device, omprt_ctx** out) {
   bool ok = cudaMalloc(&c->status_dev, 256) == cudaSuccess &&
             cudaMalloc(&c->slots_dev, kSlotBytes * OMPRT_SLOTS) == cudaSuccess &&
             cudaMalloc(&c->pool_dev, (size_t)OMPRT_MAX_RED_TEAMS * OMPRT_POOL_BYTES_PER_TEAM) ==
+                cudaSuccess &&
+            cudaMalloc(&c->mlp_rows_dev, sizeof(float) * kMlpMaxBatch * kMlpRowFloats) ==
                 cudaSuccess;
   ok = ok && cudaMemset(c->status_dev, 0, 256) == cudaSuccess &&
        cudaMemset(c->slots_dev, 0, kSlotBytes * OMPRT_SLOTS) == cudaSuccess &&
@@ -191,6 +193,7 @@ omprt_status omprt_init(int device, omprt_ctx** out) {
     cudaFree(c->status_dev);
     cudaFree(c->slots_dev);
     cudaFree(c->pool_dev);
+    cudaFree(c->mlp_rows_dev);
     cudaGetLastError();
     delete c;
     return OMPRT_ERR_NOMEM;
@@ -205,6 +208,7 @@ omprt_status omprt_finalize(omprt_ctx* c) {
   cudaFree(c->status_dev);
   cudaFree(c->slots_dev);
   cudaFree(c->pool_dev);
+  cudaFree(c->mlp_rows_dev);
   delete c;
   return OMPRT_OK;
 }

@@ -15,6 +15,7 @@ struct omprt_ctx {
   uint32_t* status_dev = nullptr;
   unsigned char* slots_dev = nullptr;
   unsigned char* pool_dev = nullptr;
+  float* mlp_rows_dev = nullptr;   // MLP per-sample scratch, kMlpMaxBatch rows
   uint32_t stack_bytes = 0;
   std::atomic<uint32_t> next_slot{0};
   // learned schedule (host copy of the model)
@@ -23,6 +24,10 @@ struct omprt_ctx {
   float feat_mean[OMPRT_MLP_IN];
   float feat_std[OMPRT_MLP_IN];
 };
+
+// MLP training batch limit and per-sample scratch row (floats).
+constexpr int kMlpMaxBatch = 16384;
+constexpr int kMlpRowFloats = 272;
 
 struct DeviceGuard {
   int prev = 0;
