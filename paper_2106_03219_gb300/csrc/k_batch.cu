@@ -65,7 +65,7 @@ __device__ __forceinline__ void run_item(const Body& b, uint64_t lo, uint64_t hi
     }
     tail = lo + nv * V;
   }
-  for (uint64_t i = tail + t; i < hi; i += T) b.one(i, acc);
+  if (tail + t < hi) run_scalar(b, tail + t, T, (hi - tail - t + T - 1) / T, acc);
 }
 
 __device__ __forceinline__ RegionArgs region_args(const BatchRegion& R) {

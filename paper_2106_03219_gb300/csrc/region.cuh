@@ -57,8 +57,10 @@ struct BodyMapRecord {
   __device__ explicit BodyMapRecord(const RegionArgs& a)
       : owner((int32_t*)a.out), count((int32_t*)a.y), last((int32_t*)a.x), id(0) {}
   __device__ bool vec_ok() const { return false; }
+  struct S1 {};
+  __device__ __forceinline__ void load1(uint64_t, S1&) const {}
   template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc&) const {
+  __device__ __forceinline__ void finish1(uint64_t i, const S1&, Acc&) const {
     owner[i] = id;
     if (count) atomicAdd(count + i, 1);
   }
@@ -77,9 +79,14 @@ struct BodyAxpyF32 {
   __device__ explicit BodyAxpyF32(const RegionArgs& r)
       : x((const float*)r.x), y((float*)r.y), a(r.alpha_f) {}
   __device__ bool vec_ok() const { return (((uintptr_t)x | (uintptr_t)y) & 31) == 0; }
+  struct S1 { float x, y; };
+  __device__ __forceinline__ void load1(uint64_t i, S1& s) const {
+    s.x = ld_nc(x + i);
+    s.y = ld_f(y + i);
+  }
   template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc& acc) const {
-    const float v = __fmaf_rn(a, __ldg(x + i), y[i]);
+  __device__ __forceinline__ void finish1(uint64_t i, const S1& s, Acc& acc) const {
+    const float v = __fmaf_rn(a, s.x, s.y);
     y[i] = v;
     acc.add(v);
   }
@@ -107,9 +114,14 @@ struct BodyAxpyI32 {
   __device__ explicit BodyAxpyI32(const RegionArgs& r)
       : x((const int32_t*)r.x), y((int32_t*)r.y), a((uint32_t)r.alpha_i) {}
   __device__ bool vec_ok() const { return (((uintptr_t)x | (uintptr_t)y) & 31) == 0; }
+  struct S1 { int32_t x, y; };
+  __device__ __forceinline__ void load1(uint64_t i, S1& s) const {
+    s.x = ld_nc(x + i);
+    s.y = ld_i(y + i);
+  }
   template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc& acc) const {
-    const int32_t v = (int32_t)(a * (uint32_t)__ldg(x + i) + (uint32_t)y[i]);
+  __device__ __forceinline__ void finish1(uint64_t i, const S1& s, Acc& acc) const {
+    const int32_t v = (int32_t)(a * (uint32_t)s.x + (uint32_t)s.y);
     y[i] = v;
     acc.add(v);
   }
@@ -136,9 +148,14 @@ struct BodyDotF32 {
   __device__ explicit BodyDotF32(const RegionArgs& r)
       : x((const float*)r.x), y((const float*)r.y) {}
   __device__ bool vec_ok() const { return (((uintptr_t)x | (uintptr_t)y) & 31) == 0; }
+  struct S1 { float x, y; };
+  __device__ __forceinline__ void load1(uint64_t i, S1& s) const {
+    s.x = ld_nc(x + i);
+    s.y = ld_nc(y + i);
+  }
   template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc& acc) const {
-    acc.add(__fmul_rn(__ldg(x + i), __ldg(y + i)));
+  __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const {
+    acc.add(__fmul_rn(s.x, s.y));
   }
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const {
     ld8_nc(x + i, f.x);
@@ -159,8 +176,10 @@ struct BodyLoadF32 {
   const float* x;
   __device__ explicit BodyLoadF32(const RegionArgs& r) : x((const float*)r.x) {}
   __device__ bool vec_ok() const { return ((uintptr_t)x & 31) == 0; }
+  struct S1 { float x; };
+  __device__ __forceinline__ void load1(uint64_t i, S1& s) const { s.x = ld_nc(x + i); }
   template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc& acc) const { acc.add(__ldg(x + i)); }
+  __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const { acc.add(s.x); }
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld8_nc(x + i, f.x); }
   template <class Acc>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
@@ -177,9 +196,11 @@ struct BodyLoadBF16 {
   const uint16_t* x;
   __device__ explicit BodyLoadBF16(const RegionArgs& r) : x((const uint16_t*)r.x) {}
   __device__ bool vec_ok() const { return ((uintptr_t)x & 31) == 0; }
+  struct S1 { uint16_t x; };
+  __device__ __forceinline__ void load1(uint64_t i, S1& s) const { s.x = ld_nc(x + i); }
   template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc& acc) const {
-    acc.add(as_f((uint32_t)ld_nc(x + i) << 16));
+  __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const {
+    acc.add(as_f((uint32_t)s.x << 16));
   }
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld8_nc(x + i, f.x); }
   template <class Acc>
@@ -199,8 +220,10 @@ struct BodyLoadI32 {
   const int32_t* x;
   __device__ explicit BodyLoadI32(const RegionArgs& r) : x((const int32_t*)r.x) {}
   __device__ bool vec_ok() const { return ((uintptr_t)x & 31) == 0; }
+  struct S1 { int32_t x; };
+  __device__ __forceinline__ void load1(uint64_t i, S1& s) const { s.x = ld_nc(x + i); }
   template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc& acc) const { acc.add(__ldg(x + i)); }
+  __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const { acc.add(s.x); }
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld8_nc(x + i, f.x); }
   template <class Acc>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
@@ -216,8 +239,10 @@ struct BodyLoadI64 {
   const int64_t* x;
   __device__ explicit BodyLoadI64(const RegionArgs& r) : x((const int64_t*)r.x) {}
   __device__ bool vec_ok() const { return ((uintptr_t)x & 31) == 0; }
+  struct S1 { int64_t x; };
+  __device__ __forceinline__ void load1(uint64_t i, S1& s) const { s.x = ld_nc(x + i); }
   template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc& acc) const { acc.add(ld_nc(x + i)); }
+  __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const { acc.add(s.x); }
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld4x64_nc(x + i, f.x); }
   template <class Acc>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
@@ -241,10 +266,18 @@ struct BodyStencil1D {
   __device__ __forceinline__ float point(float w, float c, float e) const {
     return __fmaf_rn(c1, __fadd_rn(w, e), __fmul_rn(c0, c));
   }
+  struct S1 { float w, c, e; bool edge; };
+  __device__ __forceinline__ void load1(uint64_t i, S1& s) const {
+    s.c = __ldg(in + i);
+    s.edge = i == 0 || i + 1 == n;
+    if (!s.edge) {
+      s.w = __ldg(in + i - 1);
+      s.e = __ldg(in + i + 1);
+    }
+  }
   template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc& acc) const {
-    const float c = __ldg(in + i);
-    const float v = (i == 0 || i + 1 == n) ? c : point(__ldg(in + i - 1), c, __ldg(in + i + 1));
+  __device__ __forceinline__ void finish1(uint64_t i, const S1& s, Acc& acc) const {
+    const float v = s.edge ? s.c : point(s.w, s.c, s.e);
     out[i] = v;
     acc.add(v);
   }
@@ -260,7 +293,7 @@ struct BodyStencil1D {
   __device__ __forceinline__ void finish(uint64_t i, Frag& f, Acc& acc) const {
     if (!f.interior) {
 #pragma unroll 1
-      for (int k = 0; k < 8; ++k) one(i + k, acc);
+      for (int k = 0; k < 8; ++k) run_one(*this, i + k, acc);
       return;
     }
     uint32_t o[8];
@@ -301,13 +334,21 @@ struct BodyStencil2D {
   __device__ __forceinline__ float point(float nn, float ss, float e, float w, float c) const {
     return __fmaf_rn(c1, __fadd_rn(__fadd_rn(nn, ss), __fadd_rn(e, w)), __fmul_rn(c0, c));
   }
-  template <class Acc>
-  __device__ __forceinline__ void one(uint64_t i, Acc& acc) const {
+  struct S1 { float nn, ss, e, w, c; bool edge; };
+  __device__ __forceinline__ void load1(uint64_t i, S1& s) const {
     const uint64_t r = row_of(i), c = i - r * nx;
-    const float ce = __ldg(in + i);
-    float v = ce;
-    if (r != 0 && c != 0 && r + 1 != ny && c + 1 != nx)
-      v = point(__ldg(in + i - nx), __ldg(in + i + nx), __ldg(in + i + 1), __ldg(in + i - 1), ce);
+    s.c = __ldg(in + i);
+    s.edge = r == 0 || c == 0 || r + 1 == ny || c + 1 == nx;
+    if (!s.edge) {
+      s.nn = __ldg(in + i - nx);
+      s.ss = __ldg(in + i + nx);
+      s.e = __ldg(in + i + 1);
+      s.w = __ldg(in + i - 1);
+    }
+  }
+  template <class Acc>
+  __device__ __forceinline__ void finish1(uint64_t i, const S1& s, Acc& acc) const {
+    const float v = s.edge ? s.c : point(s.nn, s.ss, s.e, s.w, s.c);
     out[i] = v;
     acc.add(v);
   }
@@ -326,7 +367,7 @@ struct BodyStencil2D {
   __device__ __forceinline__ void finish(uint64_t i, Frag& f, Acc& acc) const {
     if (!f.interior) {
 #pragma unroll 1
-      for (int k = 0; k < 8; ++k) one(i + k, acc);
+      for (int k = 0; k < 8; ++k) run_one(*this, i + k, acc);
       return;
     }
     uint32_t o[8];
@@ -346,6 +387,31 @@ struct BodyStencil2D {
 // Schedule runners.
 // ---------------------------------------------------------------------------
 
+// One iteration through the two-phase scalar interface.
+template <class Body, class Acc>
+__device__ __forceinline__ void run_one(const Body& b, uint64_t i, Acc& acc) {
+  typename Body::S1 s;
+  b.load1(i, s);
+  b.finish1(i, s, acc);
+}
+
+// Scalar iterations base, base + step, ... (cnt of them) in groups of kU:
+// all loads of a group are issued before any of its stores.
+constexpr int kU = 4;
+template <class Body, class Acc>
+__device__ __forceinline__ void run_scalar(const Body& b, uint64_t base, uint64_t step,
+                                           uint64_t cnt, Acc& acc) {
+  uint64_t k = 0;
+  for (; k + kU <= cnt; k += kU) {
+    typename Body::S1 s[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) b.load1(base + (k + u) * step, s[u]);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) b.finish1(base + (k + u) * step, s[u], acc);
+  }
+  for (; k < cnt; ++k) run_one(b, base + k * step, acc);
+}
+
 template <class Body, class = void>
 struct InFlight { static constexpr int value = 2; };
 template <class Body>
@@ -360,7 +426,9 @@ __device__ __forceinline__ void run_range(const Body& b, uint64_t a, uint64_t e,
   if constexpr (Body::kVec) {
     constexpr uint64_t V = Body::VEC;
     if (e - a >= V && b.vec_ok()) {
-      while (a % V) b.one(a++, acc);
+      const uint64_t head = (V - a % V) % V;
+      run_scalar(b, a, 1, head, acc);
+      a += head;
       typename Body::Frag f0, f1;
       if constexpr (InFlight<Body>::value >= 2) {
         for (; a + 2 * V <= e; a += 2 * V) {
@@ -376,16 +444,14 @@ __device__ __forceinline__ void run_range(const Body& b, uint64_t a, uint64_t e,
       }
     }
   }
-  for (; a < e; ++a) b.one(a, acc);
+  run_scalar(b, a, 1, e - a, acc);
 }
 
 // schedule(static, 1) inside a block: iterations base + t, base + t + T, ...
 template <class Body, class Acc>
 __device__ __forceinline__ void run_strided(const Body& b, uint64_t base, uint64_t cnt, uint32_t t,
                                             uint32_t T, Acc& acc) {
-  uint64_t j = t;
-#pragma unroll 4
-  for (; j < cnt; j += T) b.one(base + j, acc);
+  if (t < cnt) run_scalar(b, base + t, T, (cnt - t + T - 1) / T, acc);
 }
 
 // schedule(auto): 32-byte vectors grid-stride over the whole loop.
@@ -415,7 +481,8 @@ __device__ __forceinline__ void run_auto(const Body& b, uint64_t n, Acc& acc) {
       tail_start = nv * V;
     }
   }
-  for (uint64_t i = tail_start + gtid; i < n; i += nthr) b.one(i, acc);
+  if (tail_start + gtid < n)
+    run_scalar(b, tail_start + gtid, nthr, (n - tail_start - gtid + nthr - 1) / nthr, acc);
 }
 
 // ---------------------------------------------------------------------------

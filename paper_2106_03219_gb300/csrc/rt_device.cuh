@@ -179,49 +179,56 @@ __device__ inline void team_free(void* p, uint64_t bytes, uint32_t* status) {
   if (threadIdx.x == 0) free_shared(p, bytes, status);
 }
 
+#ifndef OMPRT_LD_HINT
+#define OMPRT_LD_HINT ".L2::256B"
+#endif
+
 // ---------------------------------------------------------------------------
 // Global-memory access helpers (inline PTX; 256-bit vectors need sm_100+).
+// Streaming loads carry the L2::256B prefetch-size hint: a thread that walks
+// its own contiguous range 32 bytes at a time still makes the L2 fetch whole
+// 256-byte blocks from DRAM, so per-thread streams keep DRAM row locality.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float ld_nc(const float* p) {
   float v;
-  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  asm("ld.global.nc" OMPRT_LD_HINT ".f32 %0, [%1];" : "=f"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ float ld_f(const float* p) {
   float v;
-  asm("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  asm("ld.global" OMPRT_LD_HINT ".f32 %0, [%1];" : "=f"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ int32_t ld_nc(const int32_t* p) {
   int32_t v;
-  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  asm("ld.global.nc" OMPRT_LD_HINT ".s32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ int32_t ld_i(const int32_t* p) {
   int32_t v;
-  asm("ld.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  asm("ld.global" OMPRT_LD_HINT ".s32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ int64_t ld_nc(const int64_t* p) {
   int64_t v;
-  asm("ld.global.nc.L1::no_allocate.s64 %0, [%1];" : "=l"(v) : "l"(p));
+  asm("ld.global.nc" OMPRT_LD_HINT ".s64 %0, [%1];" : "=l"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ uint16_t ld_nc(const uint16_t* p) {
   uint16_t v;
-  asm("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  asm("ld.global.nc" OMPRT_LD_HINT ".u16 %0, [%1];" : "=h"(v) : "l"(p));
   return v;
 }
 
 // 32 bytes = 8 x 32-bit
 __device__ __forceinline__ void ld8_nc(const void* p, uint32_t (&r)[8]) {
-  asm("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+  asm("ld.global.nc.L1::no_allocate" OMPRT_LD_HINT ".v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7])
       : "l"(p));
 }
 __device__ __forceinline__ void ld8(const void* p, uint32_t (&r)[8]) {
-  asm("ld.global.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+  asm("ld.global.L1::no_allocate" OMPRT_LD_HINT ".v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7])
       : "l"(p));
@@ -234,7 +241,7 @@ __device__ __forceinline__ void st8(void* p, const uint32_t (&r)[8]) {
 }
 // 32 bytes = 4 x 64-bit
 __device__ __forceinline__ void ld4x64_nc(const void* p, uint64_t (&r)[4]) {
-  asm("ld.global.nc.L1::no_allocate.v4.b64 {%0,%1,%2,%3}, [%4];"
+  asm("ld.global.nc.L1::no_allocate" OMPRT_LD_HINT ".v4.b64 {%0,%1,%2,%3}, [%4];"
       : "=l"(r[0]), "=l"(r[1]), "=l"(r[2]), "=l"(r[3])
       : "l"(p));
 }

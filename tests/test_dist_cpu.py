@@ -1,0 +1,49 @@
+"""The benchmark's multi-rank host logic on CPU: two gloo ranks agree on the
+maximum time over ranks (what bench.py divides the whole-job bytes by)."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        assert bench.dist_env() == (ws, rank, rank)
+        t = bench.max_over_ranks(10.0 + 3.5 * rank, ws)
+        bench.barrier(ws)
+        q.put((rank, t))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    assert got == {0: 13.5, 1: 13.5}
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(7.25, 1) == 7.25
