@@ -224,6 +224,38 @@ const char *omprt_status_str(omprt_status s);
 int32_t omprt_sm_count(const omprt_ctx *ctx);
 
 /* ------------------------------------------------------------------ */
+/* Reduction without any allocation                                    */
+/* ------------------------------------------------------------------ */
+/* The paper has no counterpart to this call; it exists for callers of this
+ * library that cannot allocate device memory: code running while a CUDA
+ * graph is being captured, inside a stream callback or an allocator hook,
+ * under a lock that cudaMalloc could need, or in a process whose device
+ * memory is owned and budgeted by another component.  It needs no context.
+ *
+ * Same operation and arguments as omprt_reduce (AUTO mapping, value body),
+ * but the per-team partials and the ticket live in one scratch array
+ * compiled into the library (256 bytes + 16 bytes per team, so 64.25 KiB at
+ * the maximum of OMPRT_NOALLOC_MAX_TEAMS teams) that every GPU which loads
+ * the library keeps until the process exits.  num_teams > OMPRT_NOALLOC_MAX_TEAMS
+ * returns OMPRT_ERR_INVALID; num_teams 0 means the maximum, thread_limit 0
+ * means 512.  The call never calls cudaMalloc, cudaFree or any allocating
+ * routine.
+ *  - The first call on a device looks up the array's device address for
+ *    that device (cudaGetSymbolAddress, with that device current); make that
+ *    first call before any stream capture.
+ *  - Every call shares the one array and clears its ticket on `stream`
+ *    before launching, so calls that overlap on the GPU (different streams,
+ *    or the same scratch used by two graphs running at once) race and give
+ *    wrong results.  Calls ordered on one stream are safe.
+ *  - The array keeps the last call's partials; nothing reads them later.
+ *  - No device status word is reported: the team stack is fixed at 4 KiB,
+ *    which always holds the call's 512 bytes of temporaries. */
+#define OMPRT_NOALLOC_MAX_TEAMS 4096
+omprt_status omprt_reduce_noalloc(int32_t op, int32_t dtype, int32_t precision,
+                                  const void *data_dev, int64_t n, void *result_dev,
+                                  int32_t num_teams, int32_t thread_limit, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Batched regions: many small target regions in one persistent kernel */
 /* ------------------------------------------------------------------ */
 /* The host calls omprt_batch_create once (it copies the region table to the

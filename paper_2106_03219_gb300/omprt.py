@@ -24,6 +24,7 @@ SLOTS = 64
 MAX_RED_TEAMS = 16384
 POOL_BYTES_PER_TEAM = 4096
 MLP_IN, MLP_HID, MLP_OUT, MLP_NPARAM = 16, 64, 12, 6028
+NOALLOC_MAX_TEAMS = 4096
 
 TYPE_CODES = {"i32": I32, "u32": U32, "i64": I64, "u64": U64}
 
@@ -59,6 +60,7 @@ def _declare(L):
         "omprt_launch_region": (st, [vp, C.POINTER(LoopDesc), i32, i64, i32, i32,
                                      C.POINTER(ReduceDesc), vp]),
         "omprt_reduce": (st, [vp, i32, i32, i32, vp, i64, vp, i32, i32, vp]),
+        "omprt_reduce_noalloc": (st, [i32, i32, i32, vp, i64, vp, i32, i32, vp]),
         "omprt_static_init_table": (st, [vp, C.POINTER(LoopDesc), i64, i32, i32, vp, vp]),
         "omprt_sync_status": (st, [vp, vp, C.POINTER(u32)]),
         "omprt_loop_trip_count": (st, [C.POINTER(LoopDesc), C.POINTER(C.c_uint64)]),
@@ -295,6 +297,16 @@ class Batch:
         if self.handle:
             check(lib().omprt_batch_destroy(self.handle), "omprt_batch_destroy")
             self.handle = None
+
+
+def reduce_noalloc(op, data, result, precision=PREC_COMP_F64, teams=0, threads=0, dtype=None,
+                   stream=None):
+    """omprt_reduce_noalloc: the reduction of Runtime.reduce with its scratch in
+    a fixed array inside the library; needs no context and allocates nothing."""
+    dt = _dtype_code(data) if dtype is None else dtype
+    check(lib().omprt_reduce_noalloc(int(op), int(dt), int(precision), _ptr(data),
+                                     int(data.numel()), _ptr(result), int(teams), int(threads),
+                                     _stream(stream)), "omprt_reduce_noalloc")
 
 
 def learned_configs():
