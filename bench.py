@@ -238,6 +238,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the reduction and batched-region measurements")
     ap.add_argument("--single", default=None,
                     help="profiling aid: only launch plan entries whose name contains this "
                          "(e.g. axpy/auto), warmup + steps times, and print their mean time")
@@ -338,6 +340,9 @@ def main():
     e2e_line = {"value": step_bytes * ws / (e2e_val * 1e-3) / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
 
+    reductions = measure_reductions(rt, R, torch, inputs) if not args.no_extras else None
+    batched_forms = measure_batched(rt) if not args.no_extras else None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -348,7 +353,8 @@ def main():
                 "dtype": "f32", "data": "synthetic", "config": config_dict(points),
                 "e2e": e2e_line, "roofline": roofline, "cpu_baseline": cpu,
                 "gpu_launches": len(plan) * args.steps, "clocks": clk,
-                "kernels": kernels, "source_hash": source_hash()}
+                "kernels": kernels, "reductions": reductions, "batched": batched_forms,
+                "source_hash": source_hash()}
         print(json.dumps(line))
     rt.close()
     if ws > 1:
@@ -380,6 +386,55 @@ def run_single(rt, torch, plan, args):
                       "GBps": nbytes / (ms * 1e-3) / 1e9}))
     rt.close()
     return 0
+
+
+def measure_reductions(rt, R, torch, inputs, n=1 << 28, reps=5):
+    """GB/s of the reduction configuration: n = 2^28 sums (fp32 uniform and
+    lognormal, bf16, int64) and fp32 max / min, shipped precision, 4 teams
+    per SM x 512 threads; inputs (0.5-2 GB) are larger than L2."""
+    import numpy as np
+    out = {}
+    sms = rt.sm_count
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    resi = torch.zeros(1, dtype=torch.int64, device="cuda")
+    peak, _ = measured_peaks()
+    cases = [("fp32_pm1_sum", lambda: inputs.f32_uniform_pm1(n, 0), R.OP_SUM, res),
+             ("fp32_lognormal_sum", lambda: inputs.f32_lognormal_signed(n, 0), R.OP_SUM, res),
+             ("bf16_sum", lambda: inputs.bf16_uniform_pm1(n, 0).view(np.int16), R.OP_SUM, res),
+             ("int64_sum", lambda: inputs.int64_uniform(n, 0), R.OP_SUM, resi)]
+    for name, gen, op, r in cases:
+        t = torch.from_numpy(gen()).cuda()
+        if name == "bf16_sum":
+            t = t.view(torch.bfloat16)
+        ops = [(name, op)] if name != "fp32_pm1_sum" else [(name, op), ("fp32_max", R.OP_MAX),
+                                                           ("fp32_min", R.OP_MIN)]
+        for label, o in ops:
+            rt.reduce(o, t, r, R.PREC_COMP_F64, 4 * sms, 512)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                rt.reduce(o, t, r, R.PREC_COMP_F64, 4 * sms, 512)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = t.numel() * t.element_size() / (ms * 1e-3) / 1e9
+            out[label] = {"ms": ms, "GBps": gbs, "frac": gbs / peak}
+        del t
+    assert rt.sync_status() == 0
+    return out
+
+
+def measure_batched(rt):
+    """Regions/s of the 4096-region batch: persistent kernel vs one launch per
+    region, eager and under CUDA graphs."""
+    from paper_2106_03219_gb300 import batched
+    from paper_2106_03219_gb300.autotune import load_batch_table
+    chunk, threads = load_batch_table()
+    rs = batched.RegionSet()
+    r = batched.time_forms(rt, rs, reps=5, chunk_elems=chunk, threads=threads)
+    del rs
+    return r
 
 
 def traffic_for(kernel):

@@ -39,6 +39,7 @@ def _declare(L):
                                       C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
         "orc_composite_table": (i32, [i64, i64, i64, i32, u64, u64, u64, vp]),
         "orc_owner_map": (i32, [u64, u64, u64, u64, vp]),
+        "orc_owner_map_dist": (i32, [u64, u64, u64, u64, u64, vp]),
         "orc_axpy_i32": (None, [u64, C.c_int32, vp, vp]),
         "orc_axpy_f32": (None, [u64, C.c_float, vp, vp]),
         "orc_stencil1d3_f32": (None, [u64, C.c_float, C.c_float, vp, vp]),
@@ -122,6 +123,13 @@ def composite_table(lb, ub, incr, idx_type, G, T, chunk=0):
 def owner_map(n, G, T, chunk=0):
     out = np.full(n, -1, dtype=np.int32)
     if lib().orc_owner_map(n, G, T, chunk, _p(out)):
+        raise OracleError("invalid")
+    return out
+
+
+def owner_map_dist(n, G, T, dist_chunk, chunk=0):
+    out = np.full(n, -1, dtype=np.int32)
+    if lib().orc_owner_map_dist(n, G, T, dist_chunk, chunk, _p(out)):
         raise OracleError("invalid")
     return out
 

@@ -10,8 +10,8 @@
  *
  * The paper names the runtime routines this oracle models but does not
  * specify their semantics:
- *   - worksharing-loop iteration division (Sec. 1, Sec. 2: "dividing loop
- *     iterations"),
+ *   - splitting a worksharing loop's iterations among threads (Sec. 1,
+ *     Sec. 2),
  *   - __kmpc_alloc_shared(uint64_t bytes) (Sec. 2.1, Listing 1),
  *   - team = thread block, team-shared variables (Sec. 3.1, "Global Shared
  *     Variables"),
@@ -203,6 +203,39 @@ int orc_owner_map(uint64_t n, uint64_t G, uint64_t T, uint64_t chunk, int32_t *o
             } else {
                 for (uint64_t j = t; j * chunk < bn; j += T) {
                     uint64_t a = j * chunk;
+                    uint64_t e = (bn - a > chunk) ? a + chunk : bn;
+                    for (uint64_t i = a; i < e; i++) owner[bs + i] = id;
+                }
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/*
+ * C3 with dist_schedule(static, d) at the team level: distribute chunk
+ * j = [j*d, min((j+1)*d, n)) belongs to team j mod G; inside each distribute
+ * chunk the team's threads split it by C1 (chunk 0) or C2 (chunk c), the
+ * chunk numbering restarting at the distribute chunk's start.  With d = T
+ * and c = 1 this is iteration i -> team (i / T) mod G, thread i mod T.
+ */
+int orc_owner_map_dist(uint64_t n, uint64_t G, uint64_t T, uint64_t d, uint64_t chunk,
+                       int32_t *owner)
+{
+    if (G == 0 || T == 0 || d == 0) return ORC_EINVAL;
+    for (uint64_t j = 0; j * d < n; j++) {
+        uint64_t g = j % G;
+        uint64_t bs = j * d;
+        uint64_t bn = (n - bs > d) ? d : n - bs;
+        for (uint64_t t = 0; t < T; t++) {
+            int32_t id = (int32_t)(g * T + t);
+            if (chunk == 0) {
+                uint64_t s, cnt;
+                orc_static_nochunk(bn, T, t, &s, &cnt);
+                for (uint64_t i = 0; i < cnt; i++) owner[bs + s + i] = id;
+            } else {
+                for (uint64_t k = t; k * chunk < bn; k += T) {
+                    uint64_t a = k * chunk;
                     uint64_t e = (bn - a > chunk) ? a + chunk : bn;
                     for (uint64_t i = a; i < e; i++) owner[bs + i] = id;
                 }

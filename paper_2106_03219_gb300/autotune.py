@@ -19,6 +19,52 @@ SCHEDULES = [("static1", 1, 1), ("static8", 1, 8), ("static64", 1, 64), ("static
              ("dynamic256", 2, 256), ("auto", 3, 0)]
 
 
+BATCH_TABLE = os.path.join(PKG, "tuned", "batch_gb300.json")
+
+
+def load_batch_table(path=BATCH_TABLE):
+    """(chunk_elems, threads) for the batched executor; (8192, 256) untuned."""
+    if not os.path.exists(path):
+        return 8192, 256
+    d = json.load(open(path))
+    return int(d["chunk_elems"]), int(d["threads"])
+
+
+def tune_batch(rt, rs, chunks=(2048, 4096, 8192, 16384, 32768, 65536), threads=(256, 512, 1024),
+               reps=5):
+    """Fastest (chunk_elems, threads) of the persistent kernel on a region set,
+    timed under a CUDA graph."""
+    import torch
+    best = None
+    rows = []
+    s = torch.cuda.Stream()
+    for c in chunks:
+        for t in threads:
+            b = rs.batch(rt, c)
+            g = torch.cuda.CUDAGraph()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                b.launch(0, t, stream=s)
+            g.replay()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.replay()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            rows.append({"chunk_elems": c, "threads": t, "ms": ms})
+            if best is None or ms < best[2]:
+                best = (c, t, ms)
+            del g
+            b.destroy()
+    assert rt.sync_status() == 0
+    return {"chunk_elems": best[0], "threads": best[1], "ms": best[2], "rows": rows}
+
+
 def load_sweep_table(path=SWEEP_TABLE):
     if not os.path.exists(path):
         return None
@@ -94,9 +140,18 @@ def main():
     ap.add_argument("--out", default=SWEEP_TABLE)
     ap.add_argument("--rows", default=None, help="also write every measured point here")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--batch", default=None, help="tune the batched executor, write here")
     args = ap.parse_args()
     torch.cuda.init()
     rt = R.Runtime(0)
+    if args.batch:
+        from . import batched
+        rs = batched.RegionSet()
+        res = tune_batch(rt, rs, reps=args.reps)
+        json.dump(res, open(args.batch, "w"), indent=1)
+        print(json.dumps({k: v for k, v in res.items() if k != "rows"}))
+        rt.close()
+        return
     rows, best = sweep(rt, reps=args.reps, log=print)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     json.dump({"device": torch.cuda.get_device_name(0), "sm_count": rt.sm_count, "best": best},

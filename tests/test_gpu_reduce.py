@@ -150,3 +150,34 @@ def test_full_size_bf16_and_int64(rt):
     ri = _res("i64")
     rt.reduce(R.OP_SUM, dev(a), ri, 0, 4 * rt.sm_count, 512)
     assert int(host(ri)[0]) == O.sum_int(a)
+
+
+def test_precision_report_full_size(rt):
+    """n = 2^28 fp32 (uniform [-1,1] and signed lognormal sigma = 3): error of
+    the three accumulation variants against the exact sum.  The shipped one
+    (compensated fp32, fp64 combine) meets the bound; all three errors are
+    written to gpurun_out/precision_report.json when that folder exists."""
+    import json
+    import os
+    out = {}
+    for kind, gen in (("pm1", inputs.f32_uniform_pm1), ("lognormal", inputs.f32_lognormal_signed)):
+        a = gen(N_FULL, 0)
+        exact, asum = O.exact_sum_f32(a), O.exact_abs_sum_f32(a)
+        ad = dev(a)
+        rec = {"exact": exact, "sum_abs": asum}
+        for prec, name in ((R.PREC_COMP_F64, "comp_f32_combine_f64"),
+                           (R.PREC_COMP_F32, "comp_f32_combine_f32"),
+                           (R.PREC_NAIVE_F32, "naive_f32")):
+            r = _res()
+            rt.reduce(R.OP_SUM, ad, r, prec, 4 * rt.sm_count, 512)
+            v = float(host(r)[0])
+            rec[name] = {"value": v, "rel_err": abs(v - exact) / abs(exact),
+                         "err_over_sum_abs": abs(v - exact) / asum}
+        ok, err, bound = fp_sum_ok(rec["comp_f32_combine_f64"]["value"], exact, asum)
+        assert ok, (kind, err, bound)
+        out[kind] = rec
+        del ad, a
+    root = os.environ.get("GRAFT_REPO_ROOT", os.getcwd())
+    if os.path.isdir(os.path.join(root, "gpurun_out")):
+        json.dump(out, open(os.path.join(root, "gpurun_out", "precision_report.json"), "w"),
+                  indent=1)

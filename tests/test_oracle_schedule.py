@@ -218,3 +218,38 @@ def test_composite_table_vs_brute(t, lb, incr):
                     assert row[5] == wrap64(lb + (bs + bn - 1) * incr)
                 assert row[6] == wrap64((bn if c == 0 else T * c) * incr)
                 assert row[7] == int(any(e == bn for (_, e) in pieces[tt]) and bn > 0)
+
+
+# -- dist_schedule(static, d) ------------------------------------------------------
+
+def brute_owner_dist(n, G, T, d, c):
+    """Deal distribute chunks of d round-robin to teams; inside each, deal
+    the threads' pieces as for a loop of that length."""
+    owner = [-1] * n
+    j = 0
+    for bs in range(0, n, d):
+        g = j % G
+        bn = min(d, n - bs)
+        for t, plist in enumerate(brute_pieces(bn, T, c)):
+            for a, e in plist:
+                for i in range(a, e):
+                    assert owner[bs + i] == -1
+                    owner[bs + i] = g * T + t
+        j += 1
+    return owner
+
+
+def test_owner_map_dist_vs_brute():
+    for n, G, T, d, c in itertools.product((0, 1, 7, 40, 97), (1, 2, 3, 5), (1, 3, 8),
+                                           (1, 4, 8, 13), (0, 1, 3)):
+        assert O.owner_map_dist(n, G, T, d, c).tolist() == brute_owner_dist(n, G, T, d, c)
+
+
+def test_owner_map_dist_spmd_closed_form():
+    # dist_schedule(static, T) with schedule(static, 1): i -> team (i/T) mod G, thread i mod T
+    n, G, T = 10000, 7, 32
+    own = O.owner_map_dist(n, G, T, T, 1)
+    i = np.arange(n)
+    assert np.array_equal(own, ((i // T) % G) * T + i % T)
+    # one distribute chunk per team covering the whole loop reduces to C3
+    assert np.array_equal(O.owner_map_dist(n, 1, T, n, 0), O.owner_map(n, 1, T, 0))
