@@ -78,9 +78,15 @@ typedef enum {
                                        per-team counter in global memory */
     OMPRT_SCHED_AUTO = 3,           /* mapping left to the runtime: grid-stride
                                        over 32-byte vectors */
-    OMPRT_SCHED_LEARNED = 4         /* schedule, chunk and teams chosen by the
+    OMPRT_SCHED_LEARNED = 4,        /* schedule, chunk and teams chosen by the
                                        context's cost model (see
                                        omprt_set_cost_model), else the heuristic */
+    OMPRT_SCHED_GUIDED = 5          /* each request takes max(c, ceil(r / 2T)) of
+                                       the r iterations of the team's block not yet
+                                       handed out (chunk c, 0 = 1); a warp claims 32
+                                       such chunks with one compare-and-swap on a
+                                       per-team counter (bounded retries; giving up
+                                       sets OMPRT_DEV_TIMEOUT) */
 } omprt_sched;
 
 typedef enum {
@@ -176,7 +182,7 @@ omprt_status omprt_alloc_shared(omprt_ctx *ctx, size_t bytes_per_team);
  *            `sched` with chunk `chunk` (chunk numbering restarts at the
  *            block start); AUTO ignores both levels and maps 32-byte vectors
  *            grid-stride.
- * num_teams: 1..2^31-1 (<= OMPRT_MAX_RED_TEAMS with a reduction or DYNAMIC),
+ * num_teams: 1..2^31-1 (<= OMPRT_MAX_RED_TEAMS with a reduction, DYNAMIC or GUIDED),
  *            0 = runtime choice; thread_limit: multiple of 32 in [32, 1024],
  *            0 = 256; chunk >= 1 for STATIC_CHUNKED / DYNAMIC, 0 for STATIC
  *            without chunk.  red may be NULL (no reduction clause).
@@ -188,6 +194,22 @@ omprt_status omprt_alloc_shared(omprt_ctx *ctx, size_t bytes_per_team);
 omprt_status omprt_launch_region(omprt_ctx *ctx, const omprt_loop_desc *desc, int32_t sched,
                                  int64_t chunk, int32_t num_teams, int32_t thread_limit,
                                  const omprt_reduce_desc *red, void *stream);
+
+/* The same region with dist_schedule(static, dist_chunk) at the team level:
+ * distribute chunk j = iterations [j*d, min((j+1)*d, n)) goes to team
+ * j mod num_teams, and inside each distribute chunk the team's threads split
+ * it by `sched` (STATIC with chunk 0 = one piece per thread, or
+ * STATIC_CHUNKED / STATIC with chunk c), chunk numbering restarting at the
+ * distribute chunk (OpenMP composite construct; the paper's runtime divides
+ * these iterations, Sec. 1, Sec. 2).  dist_chunk = thread_limit with chunk 1
+ * is the mapping iteration i -> team (i / T) mod G, thread i mod T.  When
+ * dist_chunk = chunk * thread_limit with chunk a multiple of 8, every thread's
+ * piece is whole 32-byte vectors.  Other schedules return
+ * OMPRT_ERR_UNSUPPORTED; dist_chunk < 1 returns OMPRT_ERR_INVALID. */
+omprt_status omprt_launch_region_dist(omprt_ctx *ctx, const omprt_loop_desc *desc,
+                                      int64_t dist_chunk, int32_t sched, int64_t chunk,
+                                      int32_t num_teams, int32_t thread_limit,
+                                      const omprt_reduce_desc *red, void *stream);
 
 /* reduction(op) over n elements of dtype (F32, BF16, I32, I64) at data_dev:
  * omprt_launch_region with BODY_NONE and schedule AUTO.  result_dev: 8 bytes

@@ -40,6 +40,7 @@ def _declare(L):
         "orc_composite_table": (i32, [i64, i64, i64, i32, u64, u64, u64, vp]),
         "orc_owner_map": (i32, [u64, u64, u64, u64, vp]),
         "orc_owner_map_dist": (i32, [u64, u64, u64, u64, u64, vp]),
+        "orc_guided_chunks": (u64, [u64, u64, u64, vp, u64]),
         "orc_axpy_i32": (None, [u64, C.c_int32, vp, vp]),
         "orc_axpy_f32": (None, [u64, C.c_float, vp, vp]),
         "orc_stencil1d3_f32": (None, [u64, C.c_float, C.c_float, vp, vp]),
@@ -132,6 +133,14 @@ def owner_map_dist(n, G, T, dist_chunk, chunk=0):
     if lib().orc_owner_map_dist(n, G, T, dist_chunk, chunk, _p(out)):
         raise OracleError("invalid")
     return out
+
+
+def guided_chunks(bn, T, chunk):
+    """Chunk starts, in hand-out order, of schedule(guided, chunk) over bn."""
+    k = lib().orc_guided_chunks(bn, T, chunk, None, 0)
+    out = np.zeros(max(k, 1), dtype=np.uint64)
+    lib().orc_guided_chunks(bn, T, chunk, _p(out), k)
+    return out[:k].astype(np.int64)
 
 
 # -- C6: bodies ----------------------------------------------------------------

@@ -245,6 +245,31 @@ int orc_owner_map_dist(uint64_t n, uint64_t G, uint64_t T, uint64_t d, uint64_t 
     return ORC_OK;
 }
 
+/*
+ * schedule(guided, c) within one team block of bn iterations and T threads.
+ * Reading: each request takes max(c, ceil(r / (2T))) of the r iterations not
+ * yet handed out, but never more than r.  The sizes depend only on r, so the
+ * partition into chunks is the same on every run; only the thread that gets
+ * each chunk varies.  Writes the chunk starts in hand-out order (at most
+ * max_chunks) and returns their number.
+ */
+uint64_t orc_guided_chunks(uint64_t bn, uint64_t T, uint64_t c, uint64_t *starts,
+                           uint64_t max_chunks)
+{
+    uint64_t next = 0, k = 0;
+    if (c == 0) c = 1;
+    while (next < bn) {
+        uint64_t r = bn - next;
+        uint64_t want = (r + 2 * T - 1) / (2 * T);
+        uint64_t size = want > c ? want : c;
+        if (size > r) size = r;
+        if (k < max_chunks) starts[k] = next;
+        k++;
+        next += size;
+    }
+    return k;
+}
+
 /* ------------------------------------------------------------------ */
 /* loop bodies (C6)                                                    */
 /* ------------------------------------------------------------------ */

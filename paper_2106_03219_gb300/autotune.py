@@ -13,7 +13,7 @@ import statistics
 PKG = os.path.dirname(os.path.abspath(__file__))
 SWEEP_TABLE = os.path.join(PKG, "tuned", "sweep_gb300.json")
 
-TEAMS = (148, 296, 592, 1184)
+TEAMS = (148, 296, 592, 1184, 2368)
 THREADS = (128, 256, 512, 1024)
 SCHEDULES = [("static1", 1, 1), ("static8", 1, 8), ("static64", 1, 64), ("static", 0, 0),
              ("dynamic256", 2, 256), ("auto", 3, 0)]

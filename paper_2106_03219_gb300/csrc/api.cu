@@ -223,9 +223,12 @@ omprt_status omprt_alloc_shared(omprt_ctx* c, size_t bytes) {
   return OMPRT_OK;
 }
 
-omprt_status omprt_launch_region(omprt_ctx* c, const omprt_loop_desc* d, int32_t sched,
-                                 int64_t chunk, int32_t teams, int32_t threads,
-                                 const omprt_reduce_desc* red, void* stream) {
+}  // extern "C"
+
+static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, int64_t dist_chunk,
+                                       int32_t sched, int64_t chunk, int32_t teams,
+                                       int32_t threads, const omprt_reduce_desc* red,
+                                       void* stream) {
   if (!c) return OMPRT_ERR_NOT_INIT;
   if (!d) return OMPRT_ERR_INVALID;
   uint64_t n;
@@ -244,10 +247,15 @@ omprt_status omprt_launch_region(omprt_ctx* c, const omprt_loop_desc* d, int32_t
     teams = cfg.teams_per_sm * c->sm_count;
     threads = cfg.threads;
   }
-  if (chunk < 0 || threads < 0 || threads > 1024 || threads % 32 || teams < 0)
+  if (chunk < 0 || threads < 0 || threads > 1024 || threads % 32 || teams < 0 || dist_chunk < 0)
     return OMPRT_ERR_INVALID;
   int ksched;
-  switch (sched) {
+  if (dist_chunk > 0) {
+    if (sched != OMPRT_SCHED_STATIC && sched != OMPRT_SCHED_STATIC_CHUNKED)
+      return OMPRT_ERR_UNSUPPORTED;
+    if (sched == OMPRT_SCHED_STATIC_CHUNKED && chunk < 1) return OMPRT_ERR_INVALID;
+    ksched = kDist;
+  } else switch (sched) {
     case OMPRT_SCHED_STATIC: ksched = chunk ? kChunked : kStatic; break;
     case OMPRT_SCHED_STATIC_CHUNKED:
       if (chunk < 1) return OMPRT_ERR_INVALID;
@@ -258,6 +266,7 @@ omprt_status omprt_launch_region(omprt_ctx* c, const omprt_loop_desc* d, int32_t
       ksched = kDynamic;
       break;
     case OMPRT_SCHED_AUTO: ksched = kAuto; break;
+    case OMPRT_SCHED_GUIDED: ksched = kGuided; break;
     default: return OMPRT_ERR_INVALID;
   }
   if (threads == 0) threads = 256;
@@ -266,14 +275,15 @@ omprt_status omprt_launch_region(omprt_ctx* c, const omprt_loop_desc* d, int32_t
     const uint64_t cap = 4ull * (uint64_t)c->sm_count;
     teams = (int32_t)(want < 1 ? 1 : (want > cap ? cap : want));
   }
-  if ((acc != kAccNone || ksched == kDynamic) && teams > OMPRT_MAX_RED_TEAMS)
-    return OMPRT_ERR_INVALID;
+  const bool counters = ksched == kDynamic || ksched == kGuided;
+  if ((acc != kAccNone || counters) && teams > OMPRT_MAX_RED_TEAMS) return OMPRT_ERR_INVALID;
 
   DeviceGuard guard(c->device);
   RegionArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = n;
   a.chunk = (uint64_t)chunk;
+  a.dist_chunk = (uint64_t)dist_chunk;
   a.x = d->x;
   a.y = d->y;
   a.out = d->out;
@@ -292,7 +302,7 @@ omprt_status omprt_launch_region(omprt_ctx* c, const omprt_loop_desc* d, int32_t
   a.pool_teams = OMPRT_MAX_RED_TEAMS;
   a.result = red ? red->result_dev : nullptr;
   a.status = c->status_dev;
-  if (acc != kAccNone || ksched == kDynamic) {
+  if (acc != kAccNone || counters) {
     ScratchSlot sl = ctx_next_slot(c);
     a.partials = sl.partials;
     a.ticket = sl.ticket;
@@ -309,6 +319,22 @@ omprt_status omprt_launch_region(omprt_ctx* c, const omprt_loop_desc* d, int32_t
     e = launch_region_f32(d->body, d->data_type, acc, ksched, (unsigned)teams, (unsigned)threads,
                           smem, st, a);
   return from_cuda(e);
+}
+
+extern "C" {
+
+omprt_status omprt_launch_region(omprt_ctx* c, const omprt_loop_desc* d, int32_t sched,
+                                 int64_t chunk, int32_t teams, int32_t threads,
+                                 const omprt_reduce_desc* red, void* stream) {
+  return launch_region_impl(c, d, 0, sched, chunk, teams, threads, red, stream);
+}
+
+omprt_status omprt_launch_region_dist(omprt_ctx* c, const omprt_loop_desc* d, int64_t dist_chunk,
+                                      int32_t sched, int64_t chunk, int32_t teams,
+                                      int32_t threads, const omprt_reduce_desc* red,
+                                      void* stream) {
+  if (dist_chunk < 1) return c ? OMPRT_ERR_INVALID : OMPRT_ERR_NOT_INIT;
+  return launch_region_impl(c, d, dist_chunk, sched, chunk, teams, threads, red, stream);
 }
 
 omprt_status omprt_reduce(omprt_ctx* c, int32_t op, int32_t dtype, int32_t precision,

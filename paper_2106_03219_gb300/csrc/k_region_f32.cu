@@ -1,5 +1,5 @@
-// Executor instances for fp32 / bf16 data: axpy, stencils, dot, value loads.
-#include "launch_common.cuh"
+// Dispatch of fp32 / bf16 region launches to the per-body instance units.
+#include "launch.h"
 
 namespace rt {
 
@@ -8,22 +8,17 @@ cudaError_t launch_region_f32(int body, int dtype, int acc, int sched, unsigned 
   switch (body) {
     case OMPRT_BODY_AXPY:
       if (dtype != OMPRT_F32) break;
-      return launch_float_accs<BodyAxpyF32>(acc, sched, grid, block, smem, st, a, true);
+      return launch_axpy(dtype, acc, sched, grid, block, smem, st, a);
     case OMPRT_BODY_STENCIL1D3:
-      if (dtype != OMPRT_F32) break;
-      return launch_float_accs<BodyStencil1D>(acc, sched, grid, block, smem, st, a, true);
     case OMPRT_BODY_STENCIL2D5:
       if (dtype != OMPRT_F32) break;
-      return launch_float_accs<BodyStencil2D>(acc, sched, grid, block, smem, st, a, true);
+      return launch_stencil(body, acc, sched, grid, block, smem, st, a);
     case OMPRT_BODY_DOT:
       if (dtype != OMPRT_F32) break;
-      return launch_float_accs<BodyDotF32>(acc, sched, grid, block, smem, st, a, false);
+      return launch_dot_load(body, dtype, acc, sched, grid, block, smem, st, a);
     case OMPRT_BODY_NONE:
-      if (dtype == OMPRT_F32)
-        return launch_float_accs<BodyLoadF32>(acc, sched, grid, block, smem, st, a, false);
-      if (dtype == OMPRT_BF16)
-        return launch_float_accs<BodyLoadBF16>(acc, sched, grid, block, smem, st, a, false);
-      break;
+      if (dtype != OMPRT_F32 && dtype != OMPRT_BF16) break;
+      return launch_dot_load(body, dtype, acc, sched, grid, block, smem, st, a);
   }
   return cudaErrorNotSupported;
 }

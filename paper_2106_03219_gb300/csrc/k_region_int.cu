@@ -11,7 +11,7 @@ cudaError_t launch_region_int(int body, int dtype, int acc, int sched, unsigned 
       return launch_sched<BodyMapRecord, AccNone>(sched, grid, block, smem, st, a);
     case OMPRT_BODY_AXPY:
       if (dtype != OMPRT_I32) break;
-      return launch_int_accs<BodyAxpyI32>(acc, sched, grid, block, smem, st, a, true);
+      return launch_axpy(dtype, acc, sched, grid, block, smem, st, a);
     case OMPRT_BODY_NONE:
       if (dtype == OMPRT_I32)
         return launch_int_accs<BodyLoadI32>(acc, sched, grid, block, smem, st, a, false);

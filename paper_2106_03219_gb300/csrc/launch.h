@@ -26,6 +26,14 @@ cudaError_t launch_region_f32(int body, int dtype, int acc, int sched, unsigned 
 cudaError_t launch_region_int(int body, int dtype, int acc, int sched, unsigned grid,
                               unsigned block, size_t smem, cudaStream_t st, const RegionArgs& a);
 
+// Per-body instance units.
+cudaError_t launch_axpy(int dtype, int acc, int sched, unsigned grid, unsigned block, size_t smem,
+                        cudaStream_t st, const RegionArgs& a);
+cudaError_t launch_stencil(int body, int acc, int sched, unsigned grid, unsigned block,
+                           size_t smem, cudaStream_t st, const RegionArgs& a);
+cudaError_t launch_dot_load(int body, int dtype, int acc, int sched, unsigned grid,
+                            unsigned block, size_t smem, cudaStream_t st, const RegionArgs& a);
+
 // Support kernels (k_support.cu).
 cudaError_t launch_static_table(uint64_t n, int64_t lb, int64_t incr, uint64_t chunk, unsigned G,
                                 unsigned T, int64_t* table, cudaStream_t st);

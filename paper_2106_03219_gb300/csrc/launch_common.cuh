@@ -25,6 +25,8 @@ inline cudaError_t launch_sched(int sched, unsigned grid, unsigned block, size_t
     case kChunked: return launch_one<Body, Acc, kChunked>(grid, block, smem, st, a);
     case kDynamic: return launch_one<Body, Acc, kDynamic>(grid, block, smem, st, a);
     case kAuto: return launch_one<Body, Acc, kAuto>(grid, block, smem, st, a);
+    case kDist: return launch_one<Body, Acc, kDist>(grid, block, smem, st, a);
+    case kGuided: return launch_one<Body, Acc, kGuided>(grid, block, smem, st, a);
   }
   return cudaErrorNotSupported;
 }

@@ -11,12 +11,22 @@
 
 namespace rt {
 
-enum : int { kStatic = 0, kChunked = 1, kDynamic = 2, kAuto = 3 };
+enum : int { kStatic = 0, kChunked = 1, kDynamic = 2, kAuto = 3, kDist = 4, kGuided = 5 };
+
+// Vectors each thread keeps in flight in the axpy body, and the largest team
+// the region kernels are compiled for (the register budget follows from it).
+#ifndef OMPRT_AXPY_INFLIGHT
+#define OMPRT_AXPY_INFLIGHT 2
+#endif
+#ifndef OMPRT_MAX_THREADS
+#define OMPRT_MAX_THREADS 1024
+#endif
 
 // Everything a region kernel needs, passed by value (one parameter block).
 struct RegionArgs {
   uint64_t n;       // trip count
-  uint64_t chunk;   // level-2 chunk (kChunked / kDynamic)
+  uint64_t chunk;   // level-2 chunk (kChunked / kDynamic / kDist; kGuided: minimum)
+  uint64_t dist_chunk;  // kDist: level-1 distribute chunk d
   const void* x;
   void* y;
   void* out;
@@ -72,6 +82,7 @@ struct BodyMapRecord {
 struct BodyAxpyF32 {
   static constexpr bool kVec = true;
   static constexpr int VEC = 8;
+  static constexpr int kInFlight = OMPRT_AXPY_INFLIGHT;
   struct Frag { uint32_t x[8], y[8]; };
   const float* x;
   float* y;
@@ -387,6 +398,13 @@ struct BodyStencil2D {
 // Schedule runners.
 // ---------------------------------------------------------------------------
 
+template <class Body, class = void>
+struct InFlight { static constexpr int value = 2; };
+template <class Body>
+struct InFlight<Body, std::void_t<decltype(Body::kInFlight)>> {
+  static constexpr int value = Body::kInFlight;
+};
+
 // One iteration through the two-phase scalar interface.
 template <class Body, class Acc>
 __device__ __forceinline__ void run_one(const Body& b, uint64_t i, Acc& acc) {
@@ -396,11 +414,15 @@ __device__ __forceinline__ void run_one(const Body& b, uint64_t i, Acc& acc) {
 }
 
 // Scalar iterations base, base + step, ... (cnt of them) in groups of kU:
-// all loads of a group are issued before any of its stores.
-constexpr int kU = 4;
+// all loads of a group are issued before any of its stores.  Bodies with
+// many operands per iteration (the 2-D stencil) use groups of 2.
+template <class Body>
+struct ScalarGroup { static constexpr int value = InFlight<Body>::value >= 2 ? 4 : 2; };
+
 template <class Body, class Acc>
 __device__ __forceinline__ void run_scalar(const Body& b, uint64_t base, uint64_t step,
                                            uint64_t cnt, Acc& acc) {
+  constexpr int kU = ScalarGroup<Body>::value;
   uint64_t k = 0;
   for (; k + kU <= cnt; k += kU) {
     typename Body::S1 s[kU];
@@ -412,12 +434,6 @@ __device__ __forceinline__ void run_scalar(const Body& b, uint64_t base, uint64_
   for (; k < cnt; ++k) run_one(b, base + k * step, acc);
 }
 
-template <class Body, class = void>
-struct InFlight { static constexpr int value = 2; };
-template <class Body>
-struct InFlight<Body, std::void_t<decltype(Body::kInFlight)>> {
-  static constexpr int value = Body::kInFlight;
-};
 
 // A contiguous range [a, e) owned by the calling thread: scalar head up to
 // vector alignment, two vectors in flight, one more vector, scalar tail.
@@ -429,18 +445,19 @@ __device__ __forceinline__ void run_range(const Body& b, uint64_t a, uint64_t e,
       const uint64_t head = (V - a % V) % V;
       run_scalar(b, a, 1, head, acc);
       a += head;
-      typename Body::Frag f0, f1;
-      if constexpr (InFlight<Body>::value >= 2) {
-        for (; a + 2 * V <= e; a += 2 * V) {
-          b.load(a, f0);
-          b.load(a + V, f1);
-          b.finish(a, f0, acc);
-          b.finish(a + V, f1, acc);
+      constexpr int N = InFlight<Body>::value;
+      typename Body::Frag f[N];
+      if constexpr (N >= 2) {
+        for (; a + N * V <= e; a += N * V) {
+#pragma unroll
+          for (int k = 0; k < N; ++k) b.load(a + k * V, f[k]);
+#pragma unroll
+          for (int k = 0; k < N; ++k) b.finish(a + k * V, f[k], acc);
         }
       }
       for (; a + V <= e; a += V) {
-        b.load(a, f0);
-        b.finish(a, f0, acc);
+        b.load(a, f[0]);
+        b.finish(a, f[0], acc);
       }
     }
   }
@@ -465,24 +482,154 @@ __device__ __forceinline__ void run_auto(const Body& b, uint64_t n, Acc& acc) {
     if (b.vec_ok()) {
       const uint64_t nv = n / V;
       uint64_t v = gtid;
-      typename Body::Frag f0, f1;
-      if constexpr (InFlight<Body>::value >= 2) {
-        for (; v + nthr < nv; v += 2 * nthr) {
-          b.load(v * V, f0);
-          b.load((v + nthr) * V, f1);
-          b.finish(v * V, f0, acc);
-          b.finish((v + nthr) * V, f1, acc);
+      constexpr int N = InFlight<Body>::value;
+      typename Body::Frag f[N];
+      if constexpr (N >= 2) {
+        for (; v + (N - 1) * nthr < nv; v += N * nthr) {
+#pragma unroll
+          for (int k = 0; k < N; ++k) b.load((v + k * nthr) * V, f[k]);
+#pragma unroll
+          for (int k = 0; k < N; ++k) b.finish((v + k * nthr) * V, f[k], acc);
         }
       }
       for (; v < nv; v += nthr) {
-        b.load(v * V, f0);
-        b.finish(v * V, f0, acc);
+        b.load(v * V, f[0]);
+        b.finish(v * V, f[0], acc);
       }
       tail_start = nv * V;
     }
   }
   if (tail_start + gtid < n)
     run_scalar(b, tail_start + gtid, nthr, (n - tail_start - gtid + nthr - 1) / nthr, acc);
+}
+
+// dist_schedule(static, d) with schedule(static, c): team g runs distribute
+// chunks g, g + G, ...; inside each the threads split it by C1 (c = 0) or C2.
+// Returns true when the calling thread runs the loop's final iteration.
+template <class Body, class Acc>
+__device__ __forceinline__ bool run_dist(const Body& b, uint64_t n, uint64_t d, uint64_t c,
+                                         uint32_t g, uint32_t G, uint32_t t, uint32_t T,
+                                         Acc& acc) {
+  const uint64_t nd = n ? (n - 1) / d + 1 : 0;
+  bool last = false;
+  uint64_t j = g;
+  if constexpr (Body::kVec) {
+    constexpr uint64_t V = Body::VEC;
+    // Fast path: d == c * T and c a multiple of the vector width, so every
+    // full distribute chunk gives each thread c / V whole aligned vectors.
+    if (InFlight<Body>::value >= 2 && c && c % V == 0 && d == c * T && b.vec_ok()) {
+      const uint64_t per = c / V;                   // vectors per thread per chunk
+      const uint64_t nfull = n / d;                 // full distribute chunks
+      const uint64_t mine = g < nfull ? (nfull - 1 - g) / G + 1 : 0;
+      const uint64_t total = mine * per;            // this thread's vectors
+      const uint64_t base = (uint64_t)t * c;
+      auto at = [=](uint64_t q) {                   // q-th vector of this thread
+        return (g + (q / per) * G) * d + base + (q % per) * V;
+      };
+      constexpr int N = InFlight<Body>::value;
+      typename Body::Frag f[N];
+      uint64_t q = 0;
+      if constexpr (N >= 2) {
+        for (; q + N <= total; q += N) {
+#pragma unroll
+          for (int k = 0; k < N; ++k) b.load(at(q + k), f[k]);
+#pragma unroll
+          for (int k = 0; k < N; ++k) b.finish(at(q + k), f[k], acc);
+        }
+      }
+      for (; q < total; ++q) {
+        const uint64_t i0 = at(q);
+        b.load(i0, f[0]);
+        b.finish(i0, f[0], acc);
+      }
+      // what is left for this team is at most the partial last chunk
+      j = (nd > nfull && nfull % G == g) ? nfull : nd;
+      // a full last chunk ends in thread T-1's piece
+      if (nd == nfull && nd && (nd - 1) % G == g && t == T - 1) last = true;
+    }
+  }
+  for (; j < nd; j += G) {
+    const uint64_t bs = j * d;
+    const uint64_t bn = n - bs > d ? d : n - bs;
+    if (c == 0) {
+      uint64_t s, cnt;
+      split_even(bn, T, t, s, cnt);
+      run_range(b, bs + s, bs + s + cnt, acc);
+      if (j == nd - 1 && cnt > 0 && s + cnt == bn) last = true;
+    } else if (c == 1) {
+      run_strided(b, bs, bn, t, T, acc);
+      if (j == nd - 1 && (bn - 1) % T == t) last = true;
+    } else {
+      const uint64_t nch = (bn - 1) / c + 1;
+      for (uint64_t k = t; k < nch; k += T) {
+        const uint64_t lo = k * c;
+        run_range(b, bs + lo, bs + (bn - lo > c ? lo + c : bn), acc);
+      }
+      if (j == nd - 1 && (nch - 1) % T == t) last = true;
+    }
+  }
+  return last;
+}
+
+// schedule(guided, c) inside the team block [bs, bs + bn): each request takes
+// max(c, ceil(r / 2T)) of the r iterations not yet handed out (never more
+// than r).  Lane 0 of a warp claims the next (up to) 32 such chunks with one
+// compare-and-swap on the team's counter; every lane then recomputes the same
+// size sequence from the claimed start and runs its own chunk.  The sizes
+// depend only on r, so the partition is the same on every run.
+__device__ __forceinline__ uint64_t guided_size(uint64_t r, uint64_t c, uint64_t twoT) {
+  const uint64_t want = (r + twoT - 1) / twoT;
+  const uint64_t s = want > c ? want : c;
+  return s < r ? s : r;
+}
+
+constexpr uint32_t kGuidedMaxTries = 1u << 20;
+
+template <class Body, class Acc>
+__device__ __forceinline__ bool run_guided(const Body& b, uint64_t bs, uint64_t bn, uint64_t c,
+                                           unsigned long long* ctr, uint32_t* status,
+                                           Acc& acc) {
+  const uint32_t lane = lane_id();
+  const uint64_t twoT = 2ull * blockDim.x;
+  bool last = false;
+  for (;;) {
+    unsigned long long base = 0;
+    int done = 0;
+    if (lane == 0) {
+      uint32_t tries = 0;
+      for (;;) {
+        const unsigned long long cur = atomicAdd(ctr, 0ull);
+        if (cur >= bn) {
+          done = 1;
+          break;
+        }
+        uint64_t pos = cur;
+        for (int k = 0; k < 32 && pos < bn; ++k) pos += guided_size(bn - pos, c, twoT);
+        if (atomicCAS(ctr, cur, (unsigned long long)pos) == cur) {
+          base = cur;
+          break;
+        }
+        if (++tries >= kGuidedMaxTries) {  // bounded: give up, report, leave the loop
+          set_status(status, OMPRT_DEV_TIMEOUT);
+          done = 1;
+          break;
+        }
+      }
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done) break;
+    base = __shfl_sync(0xffffffffu, base, 0);
+    uint64_t pos = base, size = 0;
+    for (uint32_t k = 0; k <= lane && pos < bn; ++k) {
+      size = guided_size(bn - pos, c, twoT);
+      if (k < lane) pos += size;
+    }
+    if (pos < bn && size) {
+      run_range(b, bs + pos, bs + pos + size, acc);
+      if (pos + size == bn) last = true;
+    }
+  }
+  return last;
 }
 
 // ---------------------------------------------------------------------------
@@ -563,7 +710,7 @@ __device__ inline void reduce_epilogue(const Acc& acc, const RegionArgs& a) {
 // The region kernel.
 // ---------------------------------------------------------------------------
 template <class Body, int SCHED, class Acc>
-__global__ void __launch_bounds__(1024) region_kernel(const RegionArgs a) {
+__global__ void __launch_bounds__(OMPRT_MAX_THREADS) region_kernel(const RegionArgs a) {
   const uint32_t g = blockIdx.x, G = gridDim.x, t = threadIdx.x, T = blockDim.x;
   Body body(a);
   Acc acc;
@@ -581,6 +728,8 @@ __global__ void __launch_bounds__(1024) region_kernel(const RegionArgs a) {
       const uint64_t gtid = (uint64_t)g * T + t, nthr = (uint64_t)G * T;
       last = a.n > 0 && (a.n - 1) % nthr == gtid;
     }
+  } else if constexpr (SCHED == kDist) {
+    last = run_dist(body, a.n, a.dist_chunk, a.chunk, g, G, t, T, acc);
   } else {
     uint64_t bs, bn;  // level 1: the team's block
     split_even(a.n, G, g, bs, bn);
@@ -602,6 +751,11 @@ __global__ void __launch_bounds__(1024) region_kernel(const RegionArgs a) {
         }
       }
       last = team_last && nch > 0 && (nch - 1) % T == t;
+    } else if constexpr (SCHED == kGuided) {
+      unsigned long long* ctr = a.dyn_next + g;
+      last = run_guided(body, bs, bn, a.chunk ? a.chunk : 1, ctr, a.status, acc) && team_last;
+      team_barrier();
+      if (t == 0) *ctr = 0;  // leave the counter at zero for the next launch
     } else {  // kDynamic: chunks of c claimed from this team's counter
       const uint64_t c = a.chunk;
       const uint64_t nch = bn ? (bn - 1) / c + 1 : 0;

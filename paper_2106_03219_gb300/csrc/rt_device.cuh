@@ -180,14 +180,16 @@ __device__ inline void team_free(void* p, uint64_t bytes, uint32_t* status) {
 }
 
 #ifndef OMPRT_LD_HINT
-#define OMPRT_LD_HINT ".L2::256B"
+#define OMPRT_LD_HINT ""
 #endif
 
 // ---------------------------------------------------------------------------
 // Global-memory access helpers (inline PTX; 256-bit vectors need sm_100+).
-// Streaming loads carry the L2::256B prefetch-size hint: a thread that walks
-// its own contiguous range 32 bytes at a time still makes the L2 fetch whole
-// 256-byte blocks from DRAM, so per-thread streams keep DRAM row locality.
+// OMPRT_LD_HINT may add a PTX L2 prefetch-size qualifier (".L2::128B",
+// ".L2::256B") to the streaming loads.  Measured on GB300 it does not speed up
+// any schedule, and with thousands of per-thread streams the 256-byte
+// prefetch nearly doubled the DRAM bytes read (blocks evicted before use), so
+// the default is no hint.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float ld_nc(const float* p) {
   float v;

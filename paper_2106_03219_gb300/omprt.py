@@ -15,7 +15,8 @@ from . import build_lib
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOT_INIT, ERR_DEVICE = \
     range(8)
 DEV_STACK_NOMEM, DEV_STACK_ORDER, DEV_TIMEOUT, DEV_BAD_ARG = 0x1, 0x2, 0x4, 0x8
-SCHED_STATIC, SCHED_STATIC_CHUNKED, SCHED_DYNAMIC, SCHED_AUTO, SCHED_LEARNED = range(5)
+SCHED_STATIC, SCHED_STATIC_CHUNKED, SCHED_DYNAMIC, SCHED_AUTO, SCHED_LEARNED, SCHED_GUIDED = \
+    range(6)
 I32, U32, I64, U64, F32, BF16, F64 = range(7)
 OP_SUM, OP_MAX, OP_MIN = range(3)
 PREC_COMP_F64, PREC_COMP_F32, PREC_NAIVE_F32 = range(3)
@@ -59,6 +60,8 @@ def _declare(L):
         "omprt_alloc_shared": (st, [vp, C.c_size_t]),
         "omprt_launch_region": (st, [vp, C.POINTER(LoopDesc), i32, i64, i32, i32,
                                      C.POINTER(ReduceDesc), vp]),
+        "omprt_launch_region_dist": (st, [vp, C.POINTER(LoopDesc), i64, i32, i64, i32, i32,
+                                          C.POINTER(ReduceDesc), vp]),
         "omprt_reduce": (st, [vp, i32, i32, i32, vp, i64, vp, i32, i32, vp]),
         "omprt_reduce_noalloc": (st, [i32, i32, i32, vp, i64, vp, i32, i32, vp]),
         "omprt_static_init_table": (st, [vp, C.POINTER(LoopDesc), i64, i32, i32, vp, vp]),
@@ -193,6 +196,13 @@ class Runtime:
         check(lib().omprt_launch_region(self.ctx, C.byref(desc), int(sched), int(chunk),
                                         int(teams), int(threads), rd, _stream(stream)),
               "omprt_launch_region")
+
+    def launch_region_dist(self, desc, dist_chunk, sched=SCHED_STATIC, chunk=0, teams=0,
+                           threads=0, red=None, stream=None):
+        rd = None if red is None else C.byref(red)
+        check(lib().omprt_launch_region_dist(self.ctx, C.byref(desc), int(dist_chunk), int(sched),
+                                             int(chunk), int(teams), int(threads), rd,
+                                             _stream(stream)), "omprt_launch_region_dist")
 
     def reduce(self, op, data, result, precision=PREC_COMP_F64, teams=0, threads=0, dtype=None,
                stream=None):

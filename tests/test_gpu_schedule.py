@@ -87,3 +87,104 @@ def test_dynamic_counters_reset_between_launches(rt):
     for _ in range(2 * R.SLOTS + 3):
         owner, count, last = _map_record(rt, 4099, 9, 64, R.SCHED_DYNAMIC, 16)
         assert np.all(count == 1)
+
+
+# -- dist_schedule(static, d) composite ---------------------------------------------
+
+DIST_CASES = [  # n, G, T, d, c  (d = c*T with c % 8 == 0 takes the vector fast path)
+    (0, 4, 32, 32, 1), (1, 3, 32, 32, 1), (10000, 7, 32, 32, 1), ((1 << 20) + 5, 148, 256, 256, 1),
+    ((1 << 20) + 5, 148, 256, 2048, 8), ((1 << 20), 148, 256, 2048, 8), (100003, 13, 96, 768, 8),
+    (100003, 13, 128, 8192, 64), (100003, 5, 64, 1000, 0), (100003, 5, 64, 1000, 3),
+    (77777, 9, 1024, 8192, 8), (5000, 200, 32, 256, 8)]
+
+
+@pytest.mark.parametrize("n,G,T,d,c", DIST_CASES)
+def test_dist_owner_map_bit_exact(rt, n, G, T, d, c):
+    import torch
+    owner = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
+    count = torch.zeros((max(n, 1),), dtype=torch.int32, device="cuda")
+    last = torch.full((G * T,), -1, dtype=torch.int32, device="cuda")
+    desc = R.loop_desc(R.BODY_MAP_RECORD, n=n, x=last, y=count, out=owner, data_type=R.I32)
+    rt.launch_region_dist(desc, d, R.SCHED_STATIC_CHUNKED if c else R.SCHED_STATIC, c, G, T)
+    assert rt.sync_status() == 0
+    own = host(owner)[:n]
+    assert np.array_equal(own, O.owner_map_dist(n, G, T, d, c))
+    assert np.all(host(count)[:n] == 1)
+    lf = host(last)
+    assert int((lf == 1).sum()) == (1 if n else 0)
+    if n:
+        assert lf[own[n - 1]] == 1
+
+
+@pytest.mark.parametrize("n,G,T,d,c", DIST_CASES)
+def test_dist_axpy_and_sum(rt, n, G, T, d, c):
+    import torch
+    from paper_2106_03219_gb300 import inputs
+    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+    xd, yd = dev(x), dev(y)
+    r = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rt.launch_region_dist(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0), d,
+                          R.SCHED_STATIC_CHUNKED if c else R.SCHED_STATIC, c, G, T,
+                          red=R.ReduceDesc(R.OP_SUM, R.PREC_COMP_F64, r.data_ptr()))
+    ynew = O.axpy_f32(3.0, x, y)
+    assert np.array_equal(host(yd).view(np.uint32), ynew.view(np.uint32))
+    exact = O.exact_sum_f32(ynew)
+    assert abs(float(host(r)[0]) - exact) <= 1e-6 * max(abs(exact), 1e-30)
+
+
+def test_dist_rejects(rt):
+    import torch
+    x = torch.zeros(64, device="cuda")
+    d = R.loop_desc(R.BODY_AXPY, n=64, x=x, y=x.clone())
+    for kw in (dict(dist_chunk=0), dict(dist_chunk=8, sched=R.SCHED_DYNAMIC, chunk=4),
+               dict(dist_chunk=8, sched=R.SCHED_AUTO)):
+        with pytest.raises(R.OmprtError):
+            rt.launch_region_dist(d, teams=2, threads=32, **kw)
+
+
+# -- schedule(guided, c) --------------------------------------------------------------
+
+GUIDED_CASES = [(0, 3, 32, 1), (1, 1, 32, 1), (1000, 4, 32, 1), (100003, 13, 128, 1),
+                (100003, 13, 128, 16), ((1 << 20) + 7, 148, 256, 1), ((1 << 20) + 7, 148, 256, 64),
+                (5000, 7, 1024, 3)]
+
+
+@pytest.mark.parametrize("n,G,T,c", GUIDED_CASES)
+def test_guided_partition_bit_exact(rt, n, G, T, c):
+    import torch
+    owner = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
+    count = torch.zeros((max(n, 1),), dtype=torch.int32, device="cuda")
+    last = torch.full((G * T,), -1, dtype=torch.int32, device="cuda")
+    desc = R.loop_desc(R.BODY_MAP_RECORD, n=n, x=last, y=count, out=owner, data_type=R.I32)
+    rt.launch_region(desc, R.SCHED_GUIDED, c, G, T)
+    assert rt.sync_status() == 0
+    own, cnt, lf = host(owner)[:n], host(count)[:n], host(last)
+    assert np.all(cnt == 1)
+    assert int((lf == 1).sum()) == (1 if n else 0)
+    if n:
+        assert lf[own[n - 1]] == 1
+    for g in range(G):
+        bs, bn = O.static_nochunk(n, G, g)
+        blk = own[bs:bs + bn]
+        assert np.all(blk // T == g)
+        # chunk boundaries = where the owner changes; must be the oracle's starts
+        if bn:
+            changes = np.flatnonzero(np.diff(blk) != 0) + 1
+            starts = np.concatenate([[0], changes])
+            assert np.array_equal(starts, O.guided_chunks(bn, T, c)), g
+
+
+@pytest.mark.parametrize("n,G,T,c", GUIDED_CASES)
+def test_guided_axpy_and_dot(rt, n, G, T, c):
+    import torch
+    from paper_2106_03219_gb300 import inputs
+    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+    xd, yd = dev(x), dev(y)
+    rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0), R.SCHED_GUIDED, c, G, T)
+    assert np.array_equal(host(yd).view(np.uint32), O.axpy_f32(3.0, x, y).view(np.uint32))
+    r = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rt.launch_region(R.loop_desc(R.BODY_DOT, n=n, x=dev(x), y=dev(y)), R.SCHED_GUIDED, c, G, T,
+                     red=R.ReduceDesc(R.OP_SUM, R.PREC_COMP_F64, r.data_ptr()))
+    exact = O.exact_dot_f32(x, y)
+    assert abs(float(host(r)[0]) - exact) <= 1e-6 * max(abs(exact), 1e-30)
+    assert rt.sync_status() == 0

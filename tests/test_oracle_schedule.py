@@ -253,3 +253,30 @@ def test_owner_map_dist_spmd_closed_form():
     assert np.array_equal(own, ((i // T) % G) * T + i % T)
     # one distribute chunk per team covering the whole loop reduces to C3
     assert np.array_equal(O.owner_map_dist(n, 1, T, n, 0), O.owner_map(n, 1, T, 0))
+
+
+# -- schedule(guided, c) -----------------------------------------------------------
+
+@pytest.mark.parametrize("bn,T,c", [(0, 4, 1), (1, 4, 1), (100, 4, 1), (1000, 8, 3),
+                                    (12345, 32, 16), (113359, 256, 1), (7, 100, 5)])
+def test_guided_partition_invariants(bn, T, c):
+    st = O.guided_chunks(bn, T, c).tolist()
+    sizes = [b - a for a, b in zip(st, st[1:] + [bn])]
+    assert sum(sizes) == bn
+    if bn:
+        assert st[0] == 0
+        assert sizes[0] == min(bn, max(c, -(-bn // (2 * T))))   # first request sees all of bn
+    assert all(s1 >= s2 for s1, s2 in zip(sizes, sizes[1:]))   # never growing
+    assert all(s >= c for s in sizes[:-1])                      # only the last may be short
+    # each size is what a request would take from the remainder at that point
+    r = bn
+    for s in sizes:
+        assert s == min(r, max(c, -(-r // (2 * T))))
+        r -= s
+
+
+def test_guided_degenerates():
+    # with c at least the block, one chunk
+    assert O.guided_chunks(500, 4, 500).tolist() == [0]
+    # one thread: chunks of ceil(r/2) down to c
+    assert O.guided_chunks(16, 1, 1).tolist() == [0, 8, 12, 14, 15]
