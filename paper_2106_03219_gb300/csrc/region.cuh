@@ -503,6 +503,66 @@ __device__ __forceinline__ void run_auto(const Body& b, uint64_t n, Acc& acc) {
     run_scalar(b, tail_start + gtid, nthr, (n - tail_start - gtid + nthr - 1) / nthr, acc);
 }
 
+// schedule(auto) for the 2-D stencil: the mapping is free, so each thread
+// takes an 8-column strip of kStripRows rows (items numbered strip-fastest,
+// so neighbouring threads take neighbouring strips) and walks down it with the
+// rows above, at and below in registers: one new 32-byte row vector per output
+// row, with the next row's load issued before the current row is computed.
+// East / west neighbours across the strip edge are scalar loads that hit the
+// sector a neighbouring thread just loaded.
+constexpr uint32_t kStripRows = 8;
+
+template <class Acc>
+__device__ __forceinline__ void run_stencil2d_strips(const BodyStencil2D& b, Acc& acc) {
+  const uint64_t nx = b.nx, ny = b.ny;
+  const uint64_t strips = nx / 8, nrb = (ny + kStripRows - 1) / kStripRows;
+  const uint64_t items = strips * nrb;
+  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t it = gtid; it < items; it += nthr) {
+    const uint64_t s = it % strips, rb = it / strips;
+    const uint64_t col0 = 8 * s;
+    const uint64_t r0 = rb * kStripRows, r1 = r0 + kStripRows < ny ? r0 + kStripRows : ny;
+    uint32_t up[8], cur[8], dn[8];
+    if (r0 >= 1) ld8_nc(b.in + (r0 - 1) * nx + col0, up);
+    ld8_nc(b.in + r0 * nx + col0, cur);
+    if (r0 + 1 < ny) ld8_nc(b.in + (r0 + 1) * nx + col0, dn);
+    for (uint64_t r = r0; r < r1; ++r) {
+      const uint64_t row = r * nx + col0;
+      const bool inner = r != 0 && r + 1 != ny;
+      float w = 0.f, e = 0.f;
+      if (inner) {
+        if (s > 0) w = __ldg(b.in + row - 1);
+        if (s + 1 < strips) e = __ldg(b.in + row + 8);
+      }
+      uint32_t dn2[8];
+      const bool more = r + 1 < r1 && r + 2 < ny;  // this strip needs row r + 2
+      if (more) ld8_nc(b.in + (r + 2) * nx + col0, dn2);
+      uint32_t o[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint64_t col = col0 + k;
+        if (!inner || col == 0 || col + 1 == nx) {
+          o[k] = cur[k];
+        } else {
+          const float W = k > 0 ? as_f(cur[k - 1]) : w;
+          const float E = k < 7 ? as_f(cur[k + 1]) : e;
+          o[k] = as_u(b.point(as_f(up[k]), as_f(dn[k]), E, W, as_f(cur[k])));
+        }
+      }
+      st8(b.out + row, o);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc.add(as_f(o[k]));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        up[k] = cur[k];
+        cur[k] = dn[k];
+        if (more) dn[k] = dn2[k];
+      }
+    }
+  }
+}
+
 // dist_schedule(static, d) with schedule(static, c): team g runs distribute
 // chunks g, g + G, ...; inside each the threads split it by C1 (c = 0) or C2.
 // Returns true when the calling thread runs the loop's final iteration.
@@ -723,7 +783,14 @@ __global__ void __launch_bounds__(OMPRT_MAX_THREADS) region_kernel(const RegionA
   bool last = false;  // this thread runs the loop's final iteration
   if constexpr (std::is_same<Body, BodyMapRecord>::value) body.id = (int32_t)(g * T + t);
   if constexpr (SCHED == kAuto) {
-    run_auto(body, a.n, acc);
+    if constexpr (std::is_same<Body, BodyStencil2D>::value) {
+      if (body.vec_ok())
+        run_stencil2d_strips(body, acc);
+      else
+        run_auto(body, a.n, acc);
+    } else {
+      run_auto(body, a.n, acc);
+    }
     if constexpr (std::is_same<Body, BodyMapRecord>::value) {
       const uint64_t gtid = (uint64_t)g * T + t, nthr = (uint64_t)G * T;
       last = a.n > 0 && (a.n - 1) % nthr == gtid;

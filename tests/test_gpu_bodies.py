@@ -87,7 +87,8 @@ def test_stencil1d_bit_exact(rt, sched, chunk, n):
 
 @pytest.mark.parametrize("sched,chunk", SCHEDS)
 @pytest.mark.parametrize("ny,nx", [(1, 1), (1, 9), (9, 1), (2, 2), (3, 5), (64, 64),
-                                   (129, 257), (67, 40), (1024, 1024)])
+                                   (129, 257), (67, 40), (1024, 1024), (5, 16), (9, 8), (2, 8),
+                                   (1, 8), (17, 24)])
 def test_stencil2d_bit_exact(rt, sched, chunk, ny, nx):
     import torch
     a = inputs.grid_f32(ny, nx, 6)
