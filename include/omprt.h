@@ -211,6 +211,24 @@ omprt_status omprt_launch_region_dist(omprt_ctx *ctx, const omprt_loop_desc *des
                                       int32_t num_teams, int32_t thread_limit,
                                       const omprt_reduce_desc *red, void *stream);
 
+/* Generic-mode (non-SPMD) region over segments (the runtime's main-thread /
+ * worker state machine and __kmpc_alloc_shared for variables the sequential
+ * code shares with a parallel region, Sec. 2.1, Listing 1):
+ *   teams distribute (static, balanced) over the nseg segments; for each of
+ *   its segments s the team's main thread globalises a double v = 0 on the
+ *   team stack, hands the parallel region to the team, all threads run
+ *   parallel for (static) over [seg_dev[s], seg_dev[s+1]) with
+ *   reduction(+: v), and after the join the main thread stores
+ *   result_dev[s] = v and releases v.
+ * desc: body DOT (v = sum x[i]*y[i]) or AXPY (y[i] = alpha*x[i] + y[i],
+ * v = sum of the new y[i]), data_type F32; its trip count n bounds the
+ * offsets (0 <= seg_dev[s] <= seg_dev[s+1] <= n, else the team stops and
+ * OMPRT_DEV_BAD_ARG is set).  seg_dev: int64[nseg + 1] device; result_dev:
+ * double[nseg] device.  num_teams 0 = SMs; thread_limit 0 = 256. */
+omprt_status omprt_launch_generic(omprt_ctx *ctx, const int64_t *seg_dev, int64_t nseg,
+                                  const omprt_loop_desc *desc, double *result_dev,
+                                  int32_t num_teams, int32_t thread_limit, void *stream);
+
 /* reduction(op) over n elements of dtype (F32, BF16, I32, I64) at data_dev:
  * omprt_launch_region with BODY_NONE and schedule AUTO.  result_dev: 8 bytes
  * (double for F32/BF16, int64 for integers).  precision: omprt_precision. */

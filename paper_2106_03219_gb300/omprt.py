@@ -62,6 +62,7 @@ def _declare(L):
                                      C.POINTER(ReduceDesc), vp]),
         "omprt_launch_region_dist": (st, [vp, C.POINTER(LoopDesc), i64, i32, i64, i32, i32,
                                           C.POINTER(ReduceDesc), vp]),
+        "omprt_launch_generic": (st, [vp, vp, i64, C.POINTER(LoopDesc), vp, i32, i32, vp]),
         "omprt_reduce": (st, [vp, i32, i32, i32, vp, i64, vp, i32, i32, vp]),
         "omprt_reduce_noalloc": (st, [i32, i32, i32, vp, i64, vp, i32, i32, vp]),
         "omprt_static_init_table": (st, [vp, C.POINTER(LoopDesc), i64, i32, i32, vp, vp]),
@@ -156,10 +157,13 @@ def loop_desc(body, n=None, x=None, y=None, out=None, *, lb=0, ub=None, incr=1, 
     ub_i = int(ub)
     lb_i = int(lb)
     to64 = lambda v: v - (1 << 64) if v >= (1 << 63) else v
-    return LoopDesc(to64(lb_i), to64(ub_i), int(incr), int(idx_type), int(body), int(data_type), 0,
-                    None if x is None else x.data_ptr(), None if y is None else y.data_ptr(),
-                    None if out is None else out.data_ptr(), float(alpha), float(c0), float(c1),
-                    int(nx), int(ny))
+    d = LoopDesc(to64(lb_i), to64(ub_i), int(incr), int(idx_type), int(body), int(data_type), 0,
+                 None if x is None else x.data_ptr(), None if y is None else y.data_ptr(),
+                 None if out is None else out.data_ptr(), float(alpha), float(c0), float(c1),
+                 int(nx), int(ny))
+    # the descriptor holds raw device pointers: keep the tensors alive with it
+    d._keep = (x, y, out)
+    return d
 
 
 class Runtime:
@@ -203,6 +207,13 @@ class Runtime:
         check(lib().omprt_launch_region_dist(self.ctx, C.byref(desc), int(dist_chunk), int(sched),
                                              int(chunk), int(teams), int(threads), rd,
                                              _stream(stream)), "omprt_launch_region_dist")
+
+    def launch_generic(self, seg, desc, result, teams=0, threads=0, stream=None):
+        """seg: int64 device tensor of nseg + 1 offsets; result: float64[nseg]."""
+        nseg = max(int(seg.numel()) - 1, 0)
+        check(lib().omprt_launch_generic(self.ctx, _ptr(seg), nseg, C.byref(desc), _ptr(result),
+                                         int(teams), int(threads), _stream(stream)),
+              "omprt_launch_generic")
 
     def reduce(self, op, data, result, precision=PREC_COMP_F64, teams=0, threads=0, dtype=None,
                stream=None):

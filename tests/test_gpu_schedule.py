@@ -183,7 +183,8 @@ def test_guided_axpy_and_dot(rt, n, G, T, c):
     rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0), R.SCHED_GUIDED, c, G, T)
     assert np.array_equal(host(yd).view(np.uint32), O.axpy_f32(3.0, x, y).view(np.uint32))
     r = torch.zeros(1, dtype=torch.float64, device="cuda")
-    rt.launch_region(R.loop_desc(R.BODY_DOT, n=n, x=dev(x), y=dev(y)), R.SCHED_GUIDED, c, G, T,
+    xs, ys = dev(x), dev(y)
+    rt.launch_region(R.loop_desc(R.BODY_DOT, n=n, x=xs, y=ys), R.SCHED_GUIDED, c, G, T,
                      red=R.ReduceDesc(R.OP_SUM, R.PREC_COMP_F64, r.data_ptr()))
     exact = O.exact_dot_f32(x, y)
     assert abs(float(host(r)[0]) - exact) <= 1e-6 * max(abs(exact), 1e-30)
