@@ -2,7 +2,10 @@
 
 The worksharing sweep times each (body, schedule) over the grid
 teams x threads and records the fastest point; the table is what the
-benchmark and the batched executor use.  Timing: CUDA events on the launching
+benchmark and the batched executor use.  The team counts include powers of
+two besides multiples of the SM count: with n a power of two they make every
+team's block start on a 32-byte boundary, so per-thread chunks are whole
+vectors.  Timing: CUDA events on the launching
 stream, median of `reps` launches, with an L2 flush (a write of a buffer
 larger than L2) before every timed launch.
 """
@@ -13,7 +16,7 @@ import statistics
 PKG = os.path.dirname(os.path.abspath(__file__))
 SWEEP_TABLE = os.path.join(PKG, "tuned", "sweep_gb300.json")
 
-TEAMS = (148, 296, 592, 1184, 2368)
+TEAMS = (148, 296, 592, 1024, 1184, 2048, 2368, 4096)
 THREADS = (128, 256, 512, 1024)
 SCHEDULES = [("static1", 1, 1), ("static8", 1, 8), ("static64", 1, 64), ("static", 0, 0),
              ("dynamic256", 2, 256), ("auto", 3, 0)]
