@@ -74,8 +74,9 @@ struct BodyMapRecord {
     owner[i] = id;
     if (count) atomicAdd(count + i, 1);
   }
+  template <bool kN = false>
   __device__ void load(uint64_t, Frag&) const {}
-  template <class Acc>
+  template <class Acc, bool kN = false>
   __device__ void finish(uint64_t, Frag&, Acc&) const {}
 };
 
@@ -101,15 +102,16 @@ struct BodyAxpyF32 {
     y[i] = v;
     acc.add(v);
   }
+  template <bool kN = false>
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const {
-    ld8_nc(x + i, f.x);
-    ld8(y + i, f.y);
+    ld8_nc<kN>(x + i, f.x);
+    ld8<kN>(y + i, f.y);
   }
-  template <class Acc>
+  template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t i, Frag& f, Acc& acc) const {
 #pragma unroll
     for (int k = 0; k < 8; ++k) f.y[k] = as_u(__fmaf_rn(a, as_f(f.x[k]), as_f(f.y[k])));
-    st8(y + i, f.y);
+    st8<kN>(y + i, f.y);
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc.add(as_f(f.y[k]));
   }
@@ -136,15 +138,16 @@ struct BodyAxpyI32 {
     y[i] = v;
     acc.add(v);
   }
+  template <bool kN = false>
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const {
-    ld8_nc(x + i, f.x);
-    ld8(y + i, f.y);
+    ld8_nc<kN>(x + i, f.x);
+    ld8<kN>(y + i, f.y);
   }
-  template <class Acc>
+  template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t i, Frag& f, Acc& acc) const {
 #pragma unroll
     for (int k = 0; k < 8; ++k) f.y[k] = a * f.x[k] + f.y[k];
-    st8(y + i, f.y);
+    st8<kN>(y + i, f.y);
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc.add((int32_t)f.y[k]);
   }
@@ -168,11 +171,12 @@ struct BodyDotF32 {
   __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const {
     acc.add(__fmul_rn(s.x, s.y));
   }
+  template <bool kN = false>
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const {
-    ld8_nc(x + i, f.x);
-    ld8_nc(y + i, f.y);
+    ld8_nc<kN>(x + i, f.x);
+    ld8_nc<kN>(y + i, f.y);
   }
-  template <class Acc>
+  template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc.add(__fmul_rn(as_f(f.x[k]), as_f(f.y[k])));
@@ -191,8 +195,9 @@ struct BodyLoadF32 {
   __device__ __forceinline__ void load1(uint64_t i, S1& s) const { s.x = ld_nc(x + i); }
   template <class Acc>
   __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const { acc.add(s.x); }
-  __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld8_nc(x + i, f.x); }
-  template <class Acc>
+  template <bool kN = false>
+  __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld8_nc<kN>(x + i, f.x); }
+  template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc.add(as_f(f.x[k]));
@@ -213,8 +218,9 @@ struct BodyLoadBF16 {
   __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const {
     acc.add(as_f((uint32_t)s.x << 16));
   }
-  __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld8_nc(x + i, f.x); }
-  template <class Acc>
+  template <bool kN = false>
+  __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld8_nc<kN>(x + i, f.x); }
+  template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -235,8 +241,9 @@ struct BodyLoadI32 {
   __device__ __forceinline__ void load1(uint64_t i, S1& s) const { s.x = ld_nc(x + i); }
   template <class Acc>
   __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const { acc.add(s.x); }
-  __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld8_nc(x + i, f.x); }
-  template <class Acc>
+  template <bool kN = false>
+  __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld8_nc<kN>(x + i, f.x); }
+  template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc.add((int32_t)f.x[k]);
@@ -254,8 +261,9 @@ struct BodyLoadI64 {
   __device__ __forceinline__ void load1(uint64_t i, S1& s) const { s.x = ld_nc(x + i); }
   template <class Acc>
   __device__ __forceinline__ void finish1(uint64_t, const S1& s, Acc& acc) const { acc.add(s.x); }
+  template <bool kN = false>
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const { ld4x64_nc(x + i, f.x); }
-  template <class Acc>
+  template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.add((int64_t)f.x[k]);
@@ -292,15 +300,16 @@ struct BodyStencil1D {
     out[i] = v;
     acc.add(v);
   }
+  template <bool kN = false>
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const {
-    ld8_nc(in + i, f.c);
+    ld8_nc<kN>(in + i, f.c);
     f.interior = i >= 1 && i + 8 < n;
     if (f.interior) {
       f.w = __ldg(in + i - 1);
       f.e = __ldg(in + i + 8);
     }
   }
-  template <class Acc>
+  template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t i, Frag& f, Acc& acc) const {
     if (!f.interior) {
 #pragma unroll 1
@@ -314,7 +323,7 @@ struct BodyStencil1D {
       const float e = k < 7 ? as_f(f.c[k + 1]) : f.e;
       o[k] = as_u(point(w, as_f(f.c[k]), e));
     }
-    st8(out + i, o);
+    st8<kN>(out + i, o);
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc.add(as_f(o[k]));
   }
@@ -363,18 +372,19 @@ struct BodyStencil2D {
     out[i] = v;
     acc.add(v);
   }
+  template <bool kN = false>
   __device__ __forceinline__ void load(uint64_t i, Frag& f) const {
     const uint64_t r = row_of(i), c = i - r * nx;
-    ld8_nc(in + i, f.c);
+    ld8_nc<kN>(in + i, f.c);
     f.interior = r >= 1 && r + 1 < ny && c >= 1 && c + 9 <= nx;
     if (f.interior) {
-      ld8_nc(in + i - nx, f.nn);
-      ld8_nc(in + i + nx, f.ss);
+      ld8_nc<kN>(in + i - nx, f.nn);
+      ld8_nc<kN>(in + i + nx, f.ss);
       f.w = __ldg(in + i - 1);
       f.e = __ldg(in + i + 8);
     }
   }
-  template <class Acc>
+  template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t i, Frag& f, Acc& acc) const {
     if (!f.interior) {
 #pragma unroll 1
@@ -388,7 +398,7 @@ struct BodyStencil2D {
       const float e = k < 7 ? as_f(f.c[k + 1]) : f.e;
       o[k] = as_u(point(as_f(f.nn[k]), as_f(f.ss[k]), e, w, as_f(f.c[k])));
     }
-    st8(out + i, o);
+    st8<kN>(out + i, o);
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc.add(as_f(o[k]));
   }
@@ -437,7 +447,7 @@ __device__ __forceinline__ void run_scalar(const Body& b, uint64_t base, uint64_
 
 // A contiguous range [a, e) owned by the calling thread: scalar head up to
 // vector alignment, two vectors in flight, one more vector, scalar tail.
-template <class Body, class Acc>
+template <class Body, class Acc, bool kN = false>
 __device__ __forceinline__ void run_range(const Body& b, uint64_t a, uint64_t e, Acc& acc) {
   if constexpr (Body::kVec) {
     constexpr uint64_t V = Body::VEC;
@@ -450,14 +460,14 @@ __device__ __forceinline__ void run_range(const Body& b, uint64_t a, uint64_t e,
       if constexpr (N >= 2) {
         for (; a + N * V <= e; a += N * V) {
 #pragma unroll
-          for (int k = 0; k < N; ++k) b.load(a + k * V, f[k]);
+          for (int k = 0; k < N; ++k) b.template load<kN>(a + k * V, f[k]);
 #pragma unroll
-          for (int k = 0; k < N; ++k) b.finish(a + k * V, f[k], acc);
+          for (int k = 0; k < N; ++k) b.template finish<Acc, kN>(a + k * V, f[k], acc);
         }
       }
       for (; a + V <= e; a += V) {
-        b.load(a, f[0]);
-        b.finish(a, f[0], acc);
+        b.template load<kN>(a, f[0]);
+        b.template finish<Acc, kN>(a, f[0], acc);
       }
     }
   }
@@ -824,6 +834,9 @@ __global__ void __launch_bounds__(OMPRT_MAX_THREADS) region_kernel(const RegionA
       team_barrier();
       if (t == 0) *ctr = 0;  // leave the counter at zero for the next launch
     } else {  // kDynamic: chunks of c claimed from this team's counter
+      // pointwise bodies stream each lane's chunk with 128-bit accesses
+      constexpr bool kNarrow = !std::is_same<Body, BodyStencil1D>::value &&
+                               !std::is_same<Body, BodyStencil2D>::value;
       const uint64_t c = a.chunk;
       const uint64_t nch = bn ? (bn - 1) / c + 1 : 0;
       unsigned long long* ctr = a.dyn_next + g;
@@ -836,7 +849,7 @@ __global__ void __launch_bounds__(OMPRT_MAX_THREADS) region_kernel(const RegionA
         const uint64_t j = base + lane;
         if (j < nch) {
           const uint64_t lo = j * c;
-          run_range(body, bs + lo, bs + (bn - lo > c ? lo + c : bn), acc);
+          run_range<Body, Acc, kNarrow>(body, bs + lo, bs + (bn - lo > c ? lo + c : bn), acc);
           if (j == nch - 1) last = team_last;
         }
       }
