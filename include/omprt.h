@@ -346,6 +346,14 @@ omprt_status omprt_test_barrier(omprt_ctx *ctx, int32_t num_teams, int32_t threa
                                 int32_t sub_threads, int32_t rounds, uint32_t *errors_dev,
                                 void *stream);
 
+/* Bounded device wait (the runtime has no unbounded wait): thread 0 of each
+ * of num_teams teams waits until *flag_dev == expect or timeout_us
+ * microseconds (1 .. 2,000,000) pass on the GPU timer; out_dev[g] = 1 if the
+ * value was seen, 0 if the wait gave up, in which case OMPRT_DEV_TIMEOUT is
+ * set in the status word.  The context stays usable after a timeout. */
+omprt_status omprt_test_wait(omprt_ctx *ctx, int32_t num_teams, const uint32_t *flag_dev,
+                             uint32_t expect, int64_t timeout_us, int32_t *out_dev, void *stream);
+
 /* Replay an alloc/free trace through the team shared-memory stack of every
  * team (__kmpc_alloc_shared, Sec. 2.1, Listing 1).  ops_dev: int64[nops][2]
  * (kind, arg): kind 0 = alloc(arg bytes), kind 1 = free of the block that

@@ -421,6 +421,16 @@ omprt_status omprt_test_barrier(omprt_ctx* c, int32_t teams, int32_t threads, in
                                        errors, (cudaStream_t)stream));
 }
 
+omprt_status omprt_test_wait(omprt_ctx* c, int32_t teams, const uint32_t* flag, uint32_t expect,
+                             int64_t timeout_us, int32_t* out, void* stream) {
+  if (!c) return OMPRT_ERR_NOT_INIT;
+  if (teams < 1 || teams > 4096 || !flag || !out || timeout_us < 1 || timeout_us > 2000000)
+    return OMPRT_ERR_INVALID;
+  DeviceGuard guard(c->device);
+  return from_cuda(launch_test_wait((unsigned)teams, flag, expect, (uint64_t)timeout_us * 1000,
+                                    out, c->status_dev, (cudaStream_t)stream));
+}
+
 omprt_status omprt_test_stack(omprt_ctx* c, int32_t teams, int64_t S, int64_t Q,
                               const int64_t* ops, int64_t nops, int64_t* out, int64_t* status_out,
                               void* stream) {

@@ -181,4 +181,17 @@ cudaError_t launch_test_stack(unsigned G, uint32_t S, uint32_t Q, unsigned char*
   return cudaGetLastError();
 }
 
+// One thread per team waits on a flag; out[g] = 1 if it was seen, 0 on timeout.
+__global__ void test_wait_kernel(const uint32_t* flag, uint32_t expect, uint64_t max_ns,
+                                 int32_t* out, uint32_t* status) {
+  if (threadIdx.x != 0) return;
+  out[blockIdx.x] = bounded_wait_eq(flag, expect, max_ns, status) ? 1 : 0;
+}
+
+cudaError_t launch_test_wait(unsigned G, const uint32_t* flag, uint32_t expect, uint64_t max_ns,
+                             int32_t* out, uint32_t* status, cudaStream_t st) {
+  test_wait_kernel<<<G, 32, 0, st>>>(flag, expect, max_ns, out, status);
+  return cudaGetLastError();
+}
+
 }  // namespace rt

@@ -41,6 +41,8 @@ cudaError_t launch_test_atomics(unsigned G, unsigned T, int reps, uint32_t e, ui
                                 uint32_t* returned, uint32_t* status, cudaStream_t st);
 cudaError_t launch_test_barrier(unsigned G, unsigned T, unsigned sub, int rounds, uint32_t* errors,
                                 cudaStream_t st);
+cudaError_t launch_test_wait(unsigned G, const uint32_t* flag, uint32_t expect, uint64_t max_ns,
+                             int32_t* out, uint32_t* status, cudaStream_t st);
 cudaError_t launch_test_stack(unsigned G, uint32_t S, uint32_t Q, unsigned char* pool,
                               const int64_t* ops, int64_t nops, int64_t* out, int64_t* status_out,
                               uint32_t* status, cudaStream_t st);

@@ -68,6 +68,25 @@ __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {
   atomicOr(status, bits);
 }
 
+// Wait until *flag == expect, for at most max_ns nanoseconds of the GPU's
+// global timer.  On expiry the timeout bit is set and false returned; the
+// caller then stops waiting (no device wait of the runtime is unbounded).
+__device__ inline bool bounded_wait_eq(const volatile uint32_t* flag, uint32_t expect,
+                                       uint64_t max_ns, uint32_t* status) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    if (*flag == expect) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > max_ns) {
+      set_status(status, OMPRT_DEV_TIMEOUT);
+      return false;
+    }
+    __nanosleep(256);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Synchronisation (Sec. 3.2): the whole team, or a named sub-team barrier
 // over `count` threads (a multiple of 32) on hardware barrier `id` (1..15).

@@ -78,6 +78,7 @@ def _declare(L):
         "omprt_test_atomics": (st, [vp, i32, i32, i32, u32, vp, vp, vp]),
         "omprt_test_barrier": (st, [vp, i32, i32, i32, i32, vp, vp]),
         "omprt_test_stack": (st, [vp, i32, i64, i64, vp, i64, vp, vp, vp]),
+        "omprt_test_wait": (st, [vp, i32, vp, u32, i64, vp, vp]),
         "omprt_mlp_forward": (st, [vp, vp, vp, i32, vp, vp]),
         "omprt_mlp_loss_grad": (st, [vp, vp, vp, vp, i32, vp, vp, vp]),
         "omprt_mlp_adam": (st, [vp, vp, vp, vp, vp, i32, i32, C.c_float, C.c_float, C.c_float,
@@ -243,6 +244,10 @@ class Runtime:
     def test_barrier(self, teams, threads, sub, rounds, errors, stream=None):
         check(lib().omprt_test_barrier(self.ctx, teams, threads, sub, rounds, _ptr(errors),
                                        _stream(stream)), "omprt_test_barrier")
+
+    def test_wait(self, teams, flag, expect, timeout_us, out, stream=None):
+        check(lib().omprt_test_wait(self.ctx, teams, _ptr(flag), int(expect), int(timeout_us),
+                                    _ptr(out), _stream(stream)), "omprt_test_wait")
 
     def test_stack(self, teams, stack_bytes, pool_bytes, ops, out, status, stream=None):
         nops = ops.shape[0] if ops is not None else 0

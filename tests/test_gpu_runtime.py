@@ -159,3 +159,22 @@ def test_graph_replay_self_resetting(rt):
         seen.add(v)
         assert abs(v - exact) <= 1e-6 * abs(exact)
     assert len(seen) == 1
+
+
+def test_bounded_wait_times_out_and_context_survives(rt):
+    """A wait on a flag that nothing sets gives up after its limit, reports
+    OMPRT_DEV_TIMEOUT through the status word, and later launches work."""
+    import torch
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.full((4,), -1, dtype=torch.int32, device="cuda")
+    rt.test_wait(4, flag, 1, 2000, out)                  # nobody ever writes 1
+    assert rt.sync_status() == R.DEV_TIMEOUT
+    assert host(out).tolist() == [0, 0, 0, 0]
+    flag.fill_(7)
+    rt.test_wait(2, flag, 7, 2000, out)                  # already set: returns at once
+    assert rt.sync_status() == 0
+    assert host(out)[:2].tolist() == [1, 1]
+    a = torch.arange(1000, dtype=torch.int64, device="cuda")
+    r = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rt.reduce(R.OP_SUM, a, r, 0, 4, 64)
+    assert int(host(r)[0]) == 999 * 1000 // 2
