@@ -342,6 +342,7 @@ def main():
 
     reductions = measure_reductions(rt, R, torch, inputs) if not args.no_extras else None
     batched_forms = measure_batched(rt) if not args.no_extras else None
+    learned_eval = measure_learned(rt) if not args.no_extras else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -354,6 +355,7 @@ def main():
                 "e2e": e2e_line, "roofline": roofline, "cpu_baseline": cpu,
                 "gpu_launches": len(plan) * args.steps, "clocks": clk,
                 "kernels": kernels, "reductions": reductions, "batched": batched_forms,
+                "learned": learned_eval,
                 "source_hash": source_hash()}
         print(json.dumps(line))
     rt.close()
@@ -435,6 +437,23 @@ def measure_batched(rt):
     r = batched.time_forms(rt, rs, reps=5, chunk_elems=chunk, threads=threads)
     del rs
     return r
+
+
+def measure_learned(rt, count=2000, seed=1):
+    """The committed cost model against the plain heuristic on held-out loops
+    (seed 1, never used in training): measured total time of each one's picks
+    and of the per-loop best of the 12 configurations."""
+    import numpy as np
+    from paper_2106_03219_gb300 import learned
+    model = learned.Model.load()
+    if model is None:
+        return None
+    buf = learned.LoopBuffers()
+    kind, n = learned.make_loops(count, seed)
+    T = learned.time_loops(rt, kind, n, buf, reps=3)
+    rep = learned.evaluate(rt, model, kind, n, T, buf)
+    del buf
+    return rep
 
 
 def traffic_for(kernel):

@@ -31,3 +31,32 @@ def test_learned_beats_heuristic_on_unseen_loops(rt):
     # with the model removed the runtime falls back to the heuristic
     d, red = learned.loop_desc(int(kind[0]), int(n[0]), buf)
     assert rt.choose_config(d, red is not None) == learned.HEURISTIC
+
+
+def test_learned_schedule_launch_is_exact(rt):
+    """OMPRT_SCHED_LEARNED: the installed model picks a configuration inside
+    the library and the loop runs under it with the same results as any
+    other schedule (bit-exact axpy, reduction within 1e-6)."""
+    import torch
+    import oracle as O
+    from paper_2106_03219_gb300 import inputs
+    model = learned.Model.load()
+    model.install(rt)
+    try:
+        for n in (1000, 1 << 16, (1 << 20) + 3):
+            x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+            xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+            r = torch.zeros(1, dtype=torch.float64, device="cuda")
+            d = R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0)
+            k = rt.choose_config(d, True)
+            assert 0 <= k < 12
+            rt.launch_region(d, R.SCHED_LEARNED, 0, 0, 0,
+                             red=R.ReduceDesc(R.OP_SUM, R.PREC_COMP_F64, r.data_ptr()))
+            ynew = O.axpy_f32(3.0, x, y)
+            torch.cuda.synchronize()
+            assert np.array_equal(yd.cpu().numpy().view(np.uint32), ynew.view(np.uint32))
+            exact = O.exact_sum_f32(ynew)
+            assert abs(float(r.cpu()[0]) - exact) <= 1e-6 * abs(exact)
+        assert rt.sync_status() == 0
+    finally:
+        rt.set_cost_model(None)
