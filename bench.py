@@ -46,13 +46,24 @@ SCHEDULES = [("static1", 1, 1), ("static8", 1, 8), ("static64", 1, 64), ("static
              ("dynamic256", 2, 256), ("auto", 3, 0)]
 
 
+def _code_only(text):
+    """Source text without C/C++ comments and whitespace, so that edits to
+    documentation do not change the hash while any code change does."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", "", text)
+
+
 def source_hash():
+    """Hash of the code of the kernels and the ABI header (profiles/traffic.json
+    figures are used only while it matches)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_03219_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "omprt.h"), "rb").read())
+            h.update(_code_only(open(os.path.join(csrc, f)).read()).encode())
+    h.update(_code_only(open(os.path.join(ROOT, "include", "omprt.h")).read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -97,7 +108,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -233,7 +244,7 @@ def config_dict(points):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -307,7 +307,8 @@ omprt_status omprt_reduce_noalloc(int32_t op, int32_t dtype, int32_t precision,
  * head and the tickets are reset by the last CTA to leave, so the launch can
  * be replayed from a CUDA graph without a memset.
  * Supported bodies: AXPY (F32), DOT (F32, needs red), STENCIL1D3 (F32);
- * sched of each region must be AUTO; desc[i].lb = 0, incr = 1 (n = ub + 1).
+ * inside a work item the CTA's threads take 32-byte vectors grid-stride
+ * (the auto mapping); desc[i].lb = 0, incr = 1 (n = ub + 1).
  * chunk_elems: elements per work item (multiple of 256, or 0 = 8192).
  * reds may be NULL; reds[i].result_dev NULL means no reduction for region i. */
 typedef struct omprt_batch omprt_batch;

@@ -426,8 +426,13 @@ __device__ __forceinline__ void run_one(const Body& b, uint64_t i, Acc& acc) {
 // Scalar iterations base, base + step, ... (cnt of them) in groups of kU:
 // all loads of a group are issued before any of its stores.  Bodies with
 // many operands per iteration (the 2-D stencil) use groups of 2.
+#ifndef OMPRT_WIDE_SCALAR_GROUP
+#define OMPRT_WIDE_SCALAR_GROUP 2
+#endif
 template <class Body>
-struct ScalarGroup { static constexpr int value = InFlight<Body>::value >= 2 ? 4 : 2; };
+struct ScalarGroup {
+  static constexpr int value = InFlight<Body>::value >= 2 ? 4 : OMPRT_WIDE_SCALAR_GROUP;
+};
 
 template <class Body, class Acc>
 __device__ __forceinline__ void run_scalar(const Body& b, uint64_t base, uint64_t step,

@@ -23,9 +23,9 @@ def test_learned_beats_heuristic_on_unseen_loops(rt):
     n = np.minimum(n, 1 << 24)
     T = learned.time_loops(rt, kind, n, buf, reps=3)
     rep = learned.evaluate(rt, model, kind, n, T, buf)
-    root = os.environ.get("GRAFT_REPO_ROOT", os.getcwd())
-    if os.path.isdir(os.path.join(root, "gpurun_out")):
-        json.dump(rep, open(os.path.join(root, "gpurun_out", "learned_gain.json"), "w"), indent=1)
+    report_dir = os.environ.get("OMPRT_REPORT_DIR")
+    if report_dir and os.path.isdir(report_dir):
+        json.dump(rep, open(os.path.join(report_dir, "learned_gain.json"), "w"), indent=1)
     assert rep["model_total_ms"] < rep["heuristic_total_ms"], rep
     assert rep["model_total_ms"] >= rep["best_total_ms"]
     # with the model removed the runtime falls back to the heuristic

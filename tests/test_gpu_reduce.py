@@ -154,10 +154,12 @@ def test_full_size_bf16_and_int64(rt):
 
 
 def test_precision_report_full_size(rt):
-    """n = 2^28 fp32 (uniform [-1,1] and signed lognormal sigma = 3): error of
-    the three accumulation variants against the exact sum.  The shipped one
+    """n = 2^28 fp32 (uniform [-1,1] and signed lognormal sigma = 3) and bf16
+    (uniform [-1,1]): error of the three accumulation variants against the
+    exact sum.  The shipped one
     (compensated fp32, fp64 combine) meets the bound; all three errors are
-    written to gpurun_out/precision_report.json when that folder exists."""
+    written to precision_report.json in the folder that OMPRT_REPORT_DIR names,
+    when it is set."""
     import json
     import os
     out = {}
@@ -178,7 +180,23 @@ def test_precision_report_full_size(rt):
         assert ok, (kind, err, bound)
         out[kind] = rec
         del ad, a
-    root = os.environ.get("GRAFT_REPO_ROOT", os.getcwd())
-    if os.path.isdir(os.path.join(root, "gpurun_out")):
-        json.dump(out, open(os.path.join(root, "gpurun_out", "precision_report.json"), "w"),
+    bits = inputs.bf16_uniform_pm1(N_FULL, 0)
+    vals = (bits.astype(np.uint32) << 16).view(np.float32)
+    exact, asum = O.exact_sum_bf16(bits), O.exact_abs_sum_f32(vals)
+    del vals
+    bd = _bf16_dev(bits)
+    rec = {"exact": exact, "sum_abs": asum}
+    for prec, name in ((R.PREC_COMP_F64, "comp_f32_combine_f64"),
+                       (R.PREC_COMP_F32, "comp_f32_combine_f32"),
+                       (R.PREC_NAIVE_F32, "naive_f32")):
+        r = _res()
+        rt.reduce(R.OP_SUM, bd, r, prec, 4 * rt.sm_count, 512)
+        v = float(host(r)[0])
+        rec[name] = {"value": v, "rel_err": abs(v - exact) / abs(exact),
+                     "err_over_sum_abs": abs(v - exact) / asum}
+    assert fp_sum_ok(rec["comp_f32_combine_f64"]["value"], exact, asum)[0]
+    out["bf16_pm1"] = rec
+    report_dir = os.environ.get("OMPRT_REPORT_DIR")
+    if report_dir and os.path.isdir(report_dir):
+        json.dump(out, open(os.path.join(report_dir, "precision_report.json"), "w"),
                   indent=1)
