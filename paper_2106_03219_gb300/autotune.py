@@ -17,7 +17,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 SWEEP_TABLE = os.path.join(PKG, "tuned", "sweep_gb300.json")
 
 TEAMS = (148, 296, 592, 1024, 1184, 2048, 2368, 4096, 8192)
-THREADS = (64, 128, 256, 512, 1024)
+THREADS = (32, 64, 128, 256, 512, 1024)
 SCHEDULES = [("static1", 1, 1), ("static8", 1, 8), ("static64", 1, 64), ("static", 0, 0),
              ("dynamic256", 2, 256), ("auto", 3, 0)]
 

@@ -223,7 +223,58 @@ omprt_status omprt_alloc_shared(omprt_ctx* c, size_t bytes) {
   return OMPRT_OK;
 }
 
+omprt_status omprt_set_stage_bytes(omprt_ctx* c, int64_t bytes) {
+  if (!c) return OMPRT_ERR_NOT_INIT;
+  if (bytes < 0 || bytes > (int64_t)c->max_smem_optin) return OMPRT_ERR_INVALID;
+  c->stage_bytes = (uint32_t)(bytes & ~int64_t(15));
+  return OMPRT_OK;
+}
+
 }  // extern "C"
+
+// Arrays a streaming body moves per iteration and their element size, for
+// the staged form of dynamic schedules (0 arrays: the body is not staged).
+struct StageShape {
+  uint32_t arrays, elem;
+};
+static StageShape stage_shape(int body, int dtype) {
+  switch (body) {
+    case OMPRT_BODY_AXPY:
+      return {2u, 4u};  // f32 or i32: x, y (y written back)
+    case OMPRT_BODY_DOT:
+      return {2u, 4u};
+    case OMPRT_BODY_NONE:
+      if (dtype == OMPRT_F32 || dtype == OMPRT_I32) return {1u, 4u};
+      if (dtype == OMPRT_BF16) return {1u, 2u};
+      if (dtype == OMPRT_I64) return {1u, 8u};
+      return {0u, 0u};
+    default:
+      return {0u, 0u};
+  }
+}
+
+// Staged pass size for a dynamic(c) launch: the largest P <= 32 chunks whose
+// buffers (every warp: P chunks of every array) fit the context's per-team
+// staging bytes, or 0 for the plain form.  Measured on GB300 (n = 2^26):
+// without a reduction staging wins from P >= 16 (axpy dynamic(256) 0.98 of
+// the copy rate against 0.64 plain) and loses below (dynamic(1024): P <= 8);
+// with a (compensated) reduction the per-element work needs many warps per
+// SM, and staging wins only with all 32 lanes busy on chunks of at most 512
+// bytes over all arrays (dot dynamic(64) +16%, sum +9%; dynamic(256) loses).
+static uint32_t stage_chunks(const omprt_ctx* c, int body, int dtype, uint64_t chunk,
+                             uint32_t threads, size_t smem_base, bool reduction) {
+  const StageShape sh = stage_shape(body, dtype);
+  if (!sh.arrays || c->stage_bytes == 0) return 0;
+  const uint64_t cb = chunk * sh.elem;
+  if (cb % 16 || cb > c->stage_bytes) return 0;
+  const uint64_t warps = threads / 32;
+  uint64_t P = c->stage_bytes / warps / (sh.arrays * cb);
+  if (P > 32) P = 32;
+  if (reduction ? (P < 32 || sh.arrays * cb > 512) : P < 16) return 0;
+  // leave room for the kernel's static shared memory
+  if (smem_base + warps * P * sh.arrays * cb + 2048 > (uint64_t)c->max_smem_optin) return 0;
+  return (uint32_t)P;
+}
 
 static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, int64_t dist_chunk,
                                        int32_t sched, int64_t chunk, int32_t teams,
@@ -308,7 +359,16 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
     a.ticket = sl.ticket;
     a.dyn_next = sl.dyn_next;
   }
-  const size_t smem = acc != kAccNone ? c->stack_bytes : 0;
+  size_t smem = acc != kAccNone ? c->stack_bytes : 0;
+  if (ksched == kDynamic) {
+    a.stage_chunks = stage_chunks(c, d->body, d->data_type, (uint64_t)chunk, (uint32_t)threads,
+                                  smem, acc != kAccNone);
+    if (a.stage_chunks) {
+      const StageShape sh = stage_shape(d->body, d->data_type);
+      a.stage_off = (uint32_t)smem;
+      smem += (size_t)(threads / 32) * a.stage_chunks * sh.arrays * (size_t)chunk * sh.elem;
+    }
+  }
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   const bool f32path = d->data_type == OMPRT_F32 || d->data_type == OMPRT_BF16;

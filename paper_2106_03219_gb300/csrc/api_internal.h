@@ -17,6 +17,7 @@ struct omprt_ctx {
   unsigned char* pool_dev = nullptr;
   float* mlp_rows_dev = nullptr;   // MLP per-sample scratch, kMlpMaxBatch rows
   uint32_t stack_bytes = 0;
+  uint32_t stage_bytes = 32768;    // per-team shared memory for staged dynamic schedules
   std::atomic<uint32_t> next_slot{0};
   // learned schedule (host copy of the model)
   bool has_model = false;

@@ -58,6 +58,7 @@ def _declare(L):
         "omprt_init": (st, [C.c_int, C.POINTER(vp)]),
         "omprt_finalize": (st, [vp]),
         "omprt_alloc_shared": (st, [vp, C.c_size_t]),
+        "omprt_set_stage_bytes": (st, [vp, i64]),
         "omprt_launch_region": (st, [vp, C.POINTER(LoopDesc), i32, i64, i32, i32,
                                      C.POINTER(ReduceDesc), vp]),
         "omprt_launch_region_dist": (st, [vp, C.POINTER(LoopDesc), i64, i32, i64, i32, i32,
@@ -194,6 +195,10 @@ class Runtime:
 
     def alloc_shared(self, nbytes):
         check(lib().omprt_alloc_shared(self.ctx, int(nbytes)), "omprt_alloc_shared")
+
+    def set_stage_bytes(self, nbytes):
+        """Per-team shared memory for staged dynamic schedules (0: plain form)."""
+        check(lib().omprt_set_stage_bytes(self.ctx, int(nbytes)), "omprt_set_stage_bytes")
 
     def launch_region(self, desc, sched=SCHED_STATIC, chunk=0, teams=0, threads=0, red=None,
                       stream=None):

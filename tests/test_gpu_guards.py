@@ -41,11 +41,12 @@ class Guarded:
 
 SCHEDS = [(R.SCHED_STATIC, 0), (R.SCHED_STATIC_CHUNKED, 1), (R.SCHED_STATIC_CHUNKED, 5),
           (R.SCHED_STATIC_CHUNKED, 64), (R.SCHED_DYNAMIC, 7), (R.SCHED_DYNAMIC, 256),
-          (R.SCHED_AUTO, 0), (R.SCHED_GUIDED, 3)]
+          (R.SCHED_DYNAMIC, 8), (R.SCHED_AUTO, 0), (R.SCHED_GUIDED, 3)]
 
 
 @pytest.mark.parametrize("sched,chunk", SCHEDS)
-@pytest.mark.parametrize("n,off", [(1, 1), (37, 3), (10007, 5), (65539, 7)])
+@pytest.mark.parametrize("n,off", [(1, 1), (37, 3), (10007, 5), (65539, 7), (4099, 0),
+                                   (65539, 0)])
 def test_axpy_and_stencils_stay_in_bounds(rt, sched, chunk, n, off):
     x = inputs.f32_uniform01(n, 0)
     y = Guarded(n, np.float32, off, inputs.f32_uniform01(n, 1))

@@ -1,0 +1,157 @@
+"""GPU parity: the staged form of dynamic schedules.
+
+Chunks claimed by a warp are moved through shared memory by bulk copies
+(P chunks per pass); the owner of every iteration is unchanged.  Axpy results
+must be bit-exact against the oracle with staging on (several pass sizes, from
+32 chunks per pass down to one) and off; integer reductions exact; fp32 / bf16
+sums within the reduction bound.  Cases cover ragged tails (a last chunk that is
+not a whole 16-byte unit), team blocks that do not start on a 16-byte boundary
+(those teams run the plain form inside the same launch), misaligned pointers
+and chunks that are not a whole number of 16-byte units (plain form)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2106_03219_gb300 import inputs
+from paper_2106_03219_gb300 import omprt as R
+from gpu_helpers import bits32, dev, fp_sum_ok, host
+
+pytestmark = pytest.mark.gpu
+
+DEFAULT_STAGE = 32768
+
+# (chunk, threads): chunks per pass with the default 32 KiB for axpy (2 arrays)
+CASES = [(256, 32),    # 16
+         (64, 32),     # 32 (the whole claim in one pass)
+         (64, 128),    # 16
+         (128, 64),    # 16
+         (8, 128),     # 32
+         (4, 96),      # 32, 16-byte chunks
+         (256, 64),    # 8: plain form
+         (6, 64),      # 24-byte chunks: plain form
+         (1000, 32)]   # 4: plain form
+
+
+@pytest.fixture
+def staged(rt):
+    yield rt
+    rt.set_stage_bytes(DEFAULT_STAGE)
+
+
+def _axpy(rt, n, G, T, chunk, x, y, alpha=3.0):
+    xd, yd = dev(x), dev(y)
+    rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=alpha), R.SCHED_DYNAMIC,
+                     chunk, G, T)
+    return host(yd)
+
+
+@pytest.mark.parametrize("chunk,T", CASES)
+@pytest.mark.parametrize("n", [0, 1, 5, 4099, 300007, (1 << 20) + 13])
+def test_axpy_f32_staged_bit_exact(staged, chunk, T, n):
+    rt = staged
+    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+    want = bits32(O.axpy_f32(3.0, x, y))
+    for G in (1, 7, 64):
+        assert np.array_equal(bits32(_axpy(rt, n, G, T, chunk, x, y)), want), G
+    rt.set_stage_bytes(0)  # plain form, same results
+    assert np.array_equal(bits32(_axpy(rt, n, 7, T, chunk, x, y)), want)
+    assert rt.sync_status() == 0
+
+
+@pytest.mark.parametrize("budget", [16, 2048, 16384, 32768, 65536, 131072])
+def test_axpy_i32_staged_budgets(staged, budget):
+    rt = staged
+    rt.set_stage_bytes(budget)
+    n = 200003
+    x, y = inputs.int32_uniform(n, 3), inputs.int32_uniform(n, 4)
+    want = O.axpy_i32(3, x, y)
+    for chunk, T in ((64, 32), (256, 64), (8, 512), (256, 32)):
+        xd, yd = dev(x), dev(y)
+        r = _res("i")
+        rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3), R.SCHED_DYNAMIC,
+                         chunk, 19, T, red=R.ReduceDesc(R.OP_SUM, 0, r.data_ptr()))
+        assert np.array_equal(host(yd), want), (chunk, T)
+        assert int(host(r)[0]) == O.sum_int(want), (chunk, T)
+    assert rt.sync_status() == 0
+
+
+def test_misaligned_pointers_run_plain(staged):
+    rt = staged
+    n = 65537
+    xb, yb = inputs.f32_uniform01(n + 8, 0), inputs.f32_uniform01(n + 8, 1)
+    for ox, oy in ((1, 0), (0, 3), (2, 2)):
+        xd, yd = dev(xb), dev(yb)
+        x, y = xd[ox:ox + n], yd[oy:oy + n]
+        x0, y0 = host(x).copy(), host(y).copy()
+        rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=x, y=y, alpha=-0.5), R.SCHED_DYNAMIC,
+                         256, 4, 32)
+        assert np.array_equal(bits32(host(y)), bits32(O.axpy_f32(-0.5, x0, y0)))
+        # elements outside the views are untouched
+        yh = host(yd)
+        assert np.array_equal(bits32(yh[:oy]), bits32(yb[:oy]))
+        assert np.array_equal(bits32(yh[oy + n:]), bits32(yb[oy + n:]))
+
+
+def _res(kind):
+    import torch
+    return torch.zeros(1, dtype=torch.float64 if kind == "f" else torch.int64, device="cuda")
+
+
+# with a reduction: staged for P = 32 and at most 512 bytes of chunk over the
+# arrays (dot c = 64 at T <= 64; sum c = 64 at T <= 128, c = 128 at T <= 64),
+# plain otherwise
+@pytest.mark.parametrize("chunk,T", [(64, 32), (64, 64), (64, 128), (128, 32), (256, 32),
+                                     (1000, 64), (6, 64)])
+@pytest.mark.parametrize("n", [1, 4099, (1 << 20) + 3])
+def test_reductions_staged(staged, chunk, T, n):
+    rt = staged
+    import torch
+    G = 11
+    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+    r = _res("f")
+    rt.launch_region(R.loop_desc(R.BODY_DOT, n=n, x=dev(x), y=dev(y)), R.SCHED_DYNAMIC, chunk,
+                     G, T, red=R.ReduceDesc(R.OP_SUM, R.PREC_COMP_F64, r.data_ptr()))
+    exact = O.exact_dot_f32(x, y)
+    assert fp_sum_ok(float(host(r)[0]), exact, exact)[0]
+    a = inputs.f32_lognormal_signed(n, 2)
+    rt.launch_region(R.loop_desc(R.BODY_NONE, n=n, x=dev(a), data_type=R.F32), R.SCHED_DYNAMIC,
+                     chunk, G, T, red=R.ReduceDesc(R.OP_SUM, R.PREC_COMP_F64, r.data_ptr()))
+    ok, err, bound = fp_sum_ok(float(host(r)[0]), O.exact_sum_f32(a), O.exact_abs_sum_f32(a))
+    assert ok, (err, bound)
+    rt.launch_region(R.loop_desc(R.BODY_NONE, n=n, x=dev(a), data_type=R.F32), R.SCHED_DYNAMIC,
+                     chunk, G, T, red=R.ReduceDesc(R.OP_MAX, 0, r.data_ptr()))
+    assert host(r)[0] == O.max_min(a, "max")
+    bits = inputs.bf16_uniform_pm1(n, 5)
+    xb = dev(bits.view(np.int16)).view(torch.bfloat16)
+    rt.launch_region(R.loop_desc(R.BODY_NONE, n=n, x=xb, data_type=R.BF16), R.SCHED_DYNAMIC,
+                     chunk, G, T, red=R.ReduceDesc(R.OP_SUM, R.PREC_COMP_F64, r.data_ptr()))
+    vals = (bits.astype(np.uint32) << 16).view(np.float32)
+    ok, err, bound = fp_sum_ok(float(host(r)[0]), O.exact_sum_bf16(bits),
+                               O.exact_abs_sum_f32(vals))
+    assert ok, (err, bound)
+    ri = _res("i")
+    for a in (inputs.int32_uniform(n, 3), inputs.int64_uniform(n, 4)):
+        dt = R.I32 if a.dtype == np.int32 else R.I64
+        rt.launch_region(R.loop_desc(R.BODY_NONE, n=n, x=dev(a), data_type=dt), R.SCHED_DYNAMIC,
+                         chunk, G, T, red=R.ReduceDesc(R.OP_SUM, 0, ri.data_ptr()))
+        assert int(host(ri)[0]) == O.sum_int(a)
+    assert rt.sync_status() == 0
+
+
+def test_full_size_axpy_staged(staged):
+    """n = 2^26 at the launch shape of the dynamic(256) bench line family."""
+    rt = staged
+    n = 1 << 26
+    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+    want = bits32(O.axpy_f32(3.0, x, y))
+    for G, T in ((4096, 32), (2048, 64), (1024, 256)):
+        assert np.array_equal(bits32(_axpy(rt, n, G, T, 256, x, y)), want), (G, T)
+    assert rt.sync_status() == 0
+
+
+def test_stage_bytes_validation(rt):
+    with pytest.raises(R.OmprtError):
+        rt.set_stage_bytes(-16)
+    with pytest.raises(R.OmprtError):
+        rt.set_stage_bytes(1 << 30)
+    rt.set_stage_bytes(DEFAULT_STAGE)
