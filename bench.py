@@ -248,7 +248,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the reduction and batched-region measurements")
     ap.add_argument("--single", default=None,
@@ -482,36 +482,64 @@ def traffic_for(kernel):
 
 def measure_e2e(rt, R, torch, inputs, plan, points, steps, launches):
     """Step time with H2D of the inputs from pinned memory and D2H of the
-    results inside the timed region."""
+    results inside the timed region, every step.
+
+    A streaming pipeline over three CUDA streams and NBUF device buffer
+    sets: step k's H2D (copy stream) overlaps earlier steps' kernels
+    (compute stream) and D2H (the link's other direction).  CUDA events
+    order H2D -> kernels -> D2H within a step, and keep step k's H2D off a
+    buffer set until step k - NBUF's D2H has read it."""
+    NBUF = 3
     hx = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 0)).pin_memory()
     hy = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 1)).pin_memory()
     hg = torch.from_numpy(inputs.grid_f32(GRID, GRID, 0)).pin_memory()
     ry = torch.empty_like(hy).pin_memory()
     ro = torch.empty_like(hg).pin_memory()
-    dx = torch.empty(N_AXPY, device="cuda")
-    dy = torch.empty(N_AXPY, device="cuda")
-    dg = torch.empty((GRID, GRID), device="cuda")
-    do = torch.empty_like(dg)
-    L = launches(dx, dy, dg, do)
-    stream = torch.cuda.current_stream()
+    bufs = []
+    for _ in range(NBUF):
+        dx = torch.empty(N_AXPY, device="cuda")
+        dy = torch.empty(N_AXPY, device="cuda")
+        dg = torch.empty((GRID, GRID), device="cuda")
+        do = torch.empty_like(dg)
+        bufs.append((dx, dy, dg, do, launches(dx, dy, dg, do)))
+    s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
 
-    def one():
-        dx.copy_(hx, non_blocking=True)
-        dy.copy_(hy, non_blocking=True)
-        dg.copy_(hg, non_blocking=True)
-        for name, _, desc, sched, chunk, G, T in L:
-            rt.launch_region(desc, sched, chunk, G, T, stream=stream)
-        ry.copy_(dy, non_blocking=True)
-        ro.copy_(do, non_blocking=True)
+    def pipeline(nsteps):
+        done_out = [None] * NBUF  # last D2H event per buffer set
+        for k in range(nsteps):
+            dx, dy, dg, do, L = bufs[k % NBUF]
+            if done_out[k % NBUF] is not None:
+                s_in.wait_event(done_out[k % NBUF])
+            with torch.cuda.stream(s_in):
+                dg.copy_(hg, non_blocking=True)
+                dx.copy_(hx, non_blocking=True)
+                dy.copy_(hy, non_blocking=True)
+            e_in = ev()
+            e_in.record(s_in)
+            s_run.wait_event(e_in)
+            for name, _, desc, sched, chunk, G, T in L:
+                rt.launch_region(desc, sched, chunk, G, T, stream=s_run)
+            e_run = ev()
+            e_run.record(s_run)
+            s_out.wait_event(e_run)
+            with torch.cuda.stream(s_out):
+                ro.copy_(do, non_blocking=True)
+                ry.copy_(dy, non_blocking=True)
+            done_out[k % NBUF] = ev()
+            done_out[k % NBUF].record(s_out)
+        return done_out
 
-    one()
+    pipeline(NBUF)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(steps):
-        one()
-    t1.record(stream)
+    t0.record(s_in)
+    last = pipeline(steps)
+    for e in last:
+        if e is not None:
+            s_out.wait_event(e)
+    t1.record(s_out)
     torch.cuda.synchronize()
     h2d = (hx.numel() + hy.numel() + hg.numel()) * 4
     d2h = (ry.numel() + ro.numel()) * 4
