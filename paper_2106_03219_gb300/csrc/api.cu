@@ -253,20 +253,23 @@ static StageShape stage_shape(int body, int dtype) {
   }
 }
 
-// Staged pass size for a dynamic(c) launch: the largest P <= 32 chunks whose
-// buffers (every warp: P chunks of every array) fit the context's per-team
-// staging bytes, or 0 for the plain form.  Measured on GB300 (n = 2^26):
-// without a reduction staging wins from P >= 16 (axpy dynamic(256) 0.98 of
-// the copy rate against 0.64 plain) and loses below (dynamic(1024): P <= 8);
-// with a (compensated) reduction the per-element work needs many warps per
-// SM, and staging wins only with all 32 lanes busy on chunks of at most 512
-// bytes over all arrays (dot dynamic(64) +16%, sum +9%; dynamic(256) loses).
+// Staged pass size for a dynamic(c) / static(c) / static launch: the largest
+// P <= 32 chunks whose buffers (every warp: P chunks of every array) fit the
+// context's per-team staging bytes, or 0 for the plain form.  Measured on
+// GB300 (n = 2^26): chunks below 256 bytes are already coalesced in the plain
+// form and lose to the per-pass overhead (static(8) axpy 0.94 staged against
+// 1.02 plain); without a reduction staging wins from P >= 16 (dynamic(256)
+// 0.97 against 0.64, static(64) 1.02 against 0.97) and loses below
+// (dynamic(1024): P <= 8); with a (compensated) reduction the per-element
+// work needs many warps per SM, and staging wins only with all 32 lanes busy
+// on chunks of at most 512 bytes over all arrays (dot dynamic(64) +16%, sum
+// +9%; dynamic(256) loses).
 static uint32_t stage_chunks(const omprt_ctx* c, int body, int dtype, uint64_t chunk,
                              uint32_t threads, size_t smem_base, bool reduction) {
   const StageShape sh = stage_shape(body, dtype);
   if (!sh.arrays || c->stage_bytes == 0) return 0;
   const uint64_t cb = chunk * sh.elem;
-  if (cb % 16 || cb > c->stage_bytes) return 0;
+  if (cb % 16 || cb < 256 || cb > c->stage_bytes) return 0;
   const uint64_t warps = threads / 32;
   uint64_t P = c->stage_bytes / warps / (sh.arrays * cb);
   if (P > 32) P = 32;
@@ -360,13 +363,21 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
     a.dyn_next = sl.dyn_next;
   }
   size_t smem = acc != kAccNone ? c->stack_bytes : 0;
-  if (ksched == kDynamic) {
-    a.stage_chunks = stage_chunks(c, d->body, d->data_type, (uint64_t)chunk, (uint32_t)threads,
-                                  smem, acc != kAccNone);
+  // staged forms of dynamic(c), static(c) and static: the chunk a warp's
+  // lanes own (static without chunk: one block of n / (G T) per thread, used
+  // only when that division is exact, so every team's block is T of them)
+  uint64_t stage_c = 0;
+  if (ksched == kDynamic || ksched == kChunked) stage_c = (uint64_t)chunk;
+  if (ksched == kStatic && n % ((uint64_t)teams * (uint64_t)threads) == 0)
+    stage_c = n / ((uint64_t)teams * (uint64_t)threads);
+  if (stage_c) {
+    a.stage_chunks = stage_chunks(c, d->body, d->data_type, stage_c, (uint32_t)threads, smem,
+                                  acc != kAccNone);
     if (a.stage_chunks) {
       const StageShape sh = stage_shape(d->body, d->data_type);
       a.stage_off = (uint32_t)smem;
-      smem += (size_t)(threads / 32) * a.stage_chunks * sh.arrays * (size_t)chunk * sh.elem;
+      if (ksched == kStatic) a.chunk = stage_c;
+      smem += (size_t)(threads / 32) * a.stage_chunks * sh.arrays * (size_t)stage_c * sh.elem;
     }
   }
   cudaStream_t st = (cudaStream_t)stream;

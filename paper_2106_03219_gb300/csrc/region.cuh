@@ -877,11 +877,13 @@ __device__ inline void reduce_epilogue(const Acc& acc, const RegionArgs& a) {
 }
 
 // ---------------------------------------------------------------------------
-// dynamic(c) for streaming bodies, staged through shared memory.
+// dynamic(c), static(c) and static for streaming bodies, staged through
+// shared memory.
 //
-// The dispatch is the plain one: each warp claims 32 consecutive chunks from
-// the team's counter and lane l owns chunk base + l, whose iterations it runs
-// in full.  Only the data movement differs.  The 32 chunks are one contiguous
+// The dispatch is the plain one: each warp takes 32 consecutive chunks (from
+// the team's counter under dynamic, by the fixed round robin under static)
+// and lane l owns chunk base + l, whose iterations it runs in full.  Only the
+// data movement differs.  The 32 chunks are one contiguous
 // range, so it is moved by bulk copies (one per array and pass of P chunks,
 // P = a.stage_chunks) into the warp's buffer; each owner lane then runs its
 // chunk's 16-byte units out of shared memory, starting at a lane-dependent
@@ -913,13 +915,31 @@ __device__ __forceinline__ bool stage_ok(const Body& b, uint64_t bs) {
   return (m & 15) == 0;
 }
 
-template <class Body, class Acc>
-__device__ void run_dynamic_staged(const Body& b, const RegionArgs& a, uint64_t bs, uint64_t bn,
-                                   unsigned long long* ctr, Acc& acc) {
+// Claim sources: the first chunk of the warp's next 32 (warp-uniform).
+// dynamic: one atomicAdd(32) on the team's counter per warp.
+struct ClaimDynamic {
+  unsigned long long* ctr;
+  __device__ __forceinline__ unsigned long long next() {
+    unsigned long long base = 0;
+    if (lane_id() == 0) base = atomicAdd(ctr, 32ull);
+    return __shfl_sync(0xffffffffu, base, 0);
+  }
+};
+// static(c): thread t owns chunks t, t + T, t + 2T, ..., so warp w's k-th
+// set is chunks k*T + 32w + lane; static without chunk is the same with one
+// chunk of bn / T per thread (used when T divides the block).
+struct ClaimStatic {
+  unsigned long long k;
+  uint32_t T, w32;
+  __device__ __forceinline__ unsigned long long next() { return (k++) * T + w32; }
+};
+
+template <class Body, class Acc, class Claim>
+__device__ void run_staged(const Body& b, const RegionArgs& a, uint64_t bs, uint64_t bn,
+                           uint64_t c, Claim claim, Acc& acc) {
   constexpr int A = Body::kStageArrays;
   constexpr uint32_t EB = Body::kElemBytes;
   constexpr uint32_t EPU = 16 / EB;  // elements per 16-byte unit
-  const uint64_t c = a.chunk;
   const uint32_t P = a.stage_chunks;
   const uint32_t cb = (uint32_t)(c * EB);  // bytes per chunk, a multiple of 16 (host check)
   const uint32_t uc = cb / 16;             // units per chunk
@@ -933,9 +953,7 @@ __device__ void run_dynamic_staged(const Body& b, const RegionArgs& a, uint64_t 
   uint32_t phase = 0;
   bool bad = false;
   while (!bad) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(ctr, 32ull);  // one claim of 32 chunks per warp
-    base = __shfl_sync(0xffffffffu, base, 0);
+    const unsigned long long base = claim.next();
     if (base >= nch) break;
     const uint32_t nclaim = (uint32_t)(nch - base < 32 ? nch - base : 32);
     for (uint32_t p0 = 0; p0 < nclaim; p0 += P) {
@@ -1035,14 +1053,29 @@ __global__ void __launch_bounds__(OMPRT_MAX_THREADS) region_kernel(const RegionA
     split_even(a.n, G, g, bs, bn);
     const bool team_last = bn > 0 && bs + bn == a.n;
     if constexpr (SCHED == kStatic) {
-      uint64_t s, cnt;
-      split_even(bn, T, t, s, cnt);
-      run_range(body, bs + s, bs + s + cnt, acc);
-      last = team_last && cnt > 0 && s + cnt == bn;
+      bool staged = false;
+      if constexpr (Stageable<Body>::value) {
+        // one chunk of bn / T per thread: the host stages only when every
+        // team's block is T chunks of a.chunk (the size its buffers are for)
+        staged = a.stage_chunks != 0 && a.chunk != 0 && bn == a.chunk * T && stage_ok(body, bs);
+        if (staged) run_staged(body, a, bs, bn, a.chunk, ClaimStatic{0ull, T, warp_id() * 32u}, acc);
+      }
+      if (!staged) {
+        uint64_t s, cnt;
+        split_even(bn, T, t, s, cnt);
+        run_range(body, bs + s, bs + s + cnt, acc);
+        last = team_last && cnt > 0 && s + cnt == bn;
+      }
     } else if constexpr (SCHED == kChunked) {
       const uint64_t c = a.chunk;
       const uint64_t nch = bn ? (bn - 1) / c + 1 : 0;
-      if (c == 1) {
+      bool staged = false;
+      if constexpr (Stageable<Body>::value) {
+        staged = a.stage_chunks != 0 && stage_ok(body, bs);
+        if (staged) run_staged(body, a, bs, bn, c, ClaimStatic{0ull, T, warp_id() * 32u}, acc);
+      }
+      if (staged) {
+      } else if (c == 1) {
         run_strided(body, bs, bn, t, T, acc);
       } else {
         for (uint64_t j = t; j < nch; j += T) {
@@ -1067,7 +1100,7 @@ __global__ void __launch_bounds__(OMPRT_MAX_THREADS) region_kernel(const RegionA
       bool staged = false;
       if constexpr (Stageable<Body>::value) {
         staged = a.stage_chunks != 0 && stage_ok(body, bs);  // uniform over the team
-        if (staged) run_dynamic_staged(body, a, bs, bn, ctr, acc);
+        if (staged) run_staged(body, a, bs, bn, c, ClaimDynamic{ctr}, acc);
       }
       while (!staged) {
         unsigned long long base = 0;

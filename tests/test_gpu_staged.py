@@ -1,6 +1,6 @@
-"""GPU parity: the staged form of dynamic schedules.
+"""GPU parity: the staged form of dynamic, static(c) and static schedules.
 
-Chunks claimed by a warp are moved through shared memory by bulk copies
+Chunks taken by a warp are moved through shared memory by bulk copies
 (P chunks per pass); the owner of every iteration is unchanged.  Axpy results
 must be bit-exact against the oracle with staging on (several pass sizes, from
 32 chunks per pass down to one) and off; integer reductions exact; fp32 / bf16
@@ -25,9 +25,9 @@ CASES = [(256, 32),    # 16
          (64, 32),     # 32 (the whole claim in one pass)
          (64, 128),    # 16
          (128, 64),    # 16
-         (8, 128),     # 32
-         (4, 96),      # 32, 16-byte chunks
+         (68, 32),     # 30: a 272-byte chunk, not a power of two
          (256, 64),    # 8: plain form
+         (8, 128),     # 32-byte chunks: plain form
          (6, 64),      # 24-byte chunks: plain form
          (1000, 32)]   # 4: plain form
 
@@ -58,6 +58,45 @@ def test_axpy_f32_staged_bit_exact(staged, chunk, T, n):
     assert rt.sync_status() == 0
 
 
+# static(c): warp w's k-th set of chunks is k*T + 32w + lane, one contiguous
+# range; static without chunk is staged when n = G * T * c exactly.
+@pytest.mark.parametrize("chunk,T", [(64, 32), (64, 128), (256, 32), (68, 64), (8, 512), (6, 64)])
+@pytest.mark.parametrize("n", [1, 4099, 300007, (1 << 20) + 13])
+def test_axpy_static_chunked_staged_bit_exact(staged, chunk, T, n):
+    rt = staged
+    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+    want = bits32(O.axpy_f32(3.0, x, y))
+    for G in (1, 7, 64):
+        xd, yd = dev(x), dev(y)
+        rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0),
+                         R.SCHED_STATIC_CHUNKED, chunk, G, T)
+        assert np.array_equal(bits32(host(yd)), want), G
+    assert rt.sync_status() == 0
+
+
+@pytest.mark.parametrize("G,T,c", [(1, 32, 256), (16, 32, 64), (64, 128, 64), (8, 64, 128),
+                                   (4, 256, 16), (2, 32, 68)])
+def test_axpy_static_staged_bit_exact(staged, G, T, c):
+    """n = G * T * c: every thread's block is one staged chunk; n + 4 and
+    n - 4 (blocks of unequal size) run the plain form."""
+    rt = staged
+    for n in (G * T * c, G * T * c + 4, G * T * c - 4):
+        x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+        xd, yd = dev(x), dev(y)
+        rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0), R.SCHED_STATIC, 0,
+                         G, T)
+        assert np.array_equal(bits32(host(yd)), bits32(O.axpy_f32(3.0, x, y))), n
+        r = _res("i")
+        xi, yi = inputs.int32_uniform(n, 3), inputs.int32_uniform(n, 4)
+        yid = dev(yi)
+        rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=dev(xi), y=yid, alpha=3), R.SCHED_STATIC,
+                         0, G, T, red=R.ReduceDesc(R.OP_SUM, 0, r.data_ptr()))
+        want = O.axpy_i32(3, xi, yi)
+        assert np.array_equal(host(yid), want), n
+        assert int(host(r)[0]) == O.sum_int(want), n
+    assert rt.sync_status() == 0
+
+
 @pytest.mark.parametrize("budget", [16, 2048, 16384, 32768, 65536, 131072])
 def test_axpy_i32_staged_budgets(staged, budget):
     rt = staged
@@ -65,7 +104,7 @@ def test_axpy_i32_staged_budgets(staged, budget):
     n = 200003
     x, y = inputs.int32_uniform(n, 3), inputs.int32_uniform(n, 4)
     want = O.axpy_i32(3, x, y)
-    for chunk, T in ((64, 32), (256, 64), (8, 512), (256, 32)):
+    for chunk, T in ((64, 32), (256, 64), (8, 512), (256, 32), (64, 512)):
         xd, yd = dev(x), dev(y)
         r = _res("i")
         rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3), R.SCHED_DYNAMIC,
