@@ -175,7 +175,7 @@ omprt_status omprt_finalize(omprt_ctx *ctx);
 omprt_status omprt_alloc_shared(omprt_ctx *ctx, size_t bytes_per_team);
 
 /* Per-team shared memory that dynamic and static schedules of streaming bodies
- * (axpy, dot, value reductions) may use to stage their chunks.  The dispatch
+ * (axpy, dot, value reductions, the stencils) may use to stage their chunks.  The dispatch
  * and the ownership are unchanged (each warp takes 32 consecutive chunks of c,
  * lane l runs chunk base + l in full, Sec. 3.1 worksharing); the range is
  * moved through shared memory by bulk copies, P chunks per pass, with
@@ -184,9 +184,12 @@ omprt_status omprt_alloc_shared(omprt_ctx *ctx, size_t bytes_per_team);
  * static without chunk when n = teams * threads * c' exactly (c' per thread).
  * A launch is staged when c * element size is a multiple of 16 and at least
  * 256, and P >= 16 (loops without a reduction), or P = 32 and c * element
- * size summed over the arrays is at most 512 (loops with one); other
- * launches, and teams whose block does not start on a 16-byte boundary, run
- * the plain form.  bytes is rounded down to
+ * size summed over the arrays is at most 512 (loops with one).  The
+ * stencils (no reduction, n and nx multiples of 4) stage an input window that
+ * reaches one element / one row beyond the pass, when the chunk is at most
+ * 512 bytes and the two halos at most a quarter of the pass.  A claim of 32
+ * chunks runs in equal passes.  Other launches, and teams whose block does
+ * not start on a 16-byte boundary, run the plain form.  bytes is rounded down to
  * 16; 0 turns staging off; more than the device's per-block shared memory is
  * OMPRT_ERR_INVALID.  Default after init: 32 KiB. */
 omprt_status omprt_set_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_team);

@@ -232,24 +232,31 @@ omprt_status omprt_set_stage_bytes(omprt_ctx* c, int64_t bytes) {
 
 }  // extern "C"
 
-// Arrays a streaming body moves per iteration and their element size, for
-// the staged form of dynamic schedules (0 arrays: the body is not staged).
+// Arrays a body moves per iteration and their element size, for the staged
+// form of schedules (0 arrays: the body is not staged); halo: elements its
+// input window reaches beyond a pass on each side (the stencils).
 struct StageShape {
   uint32_t arrays, elem;
+  uint64_t halo;
 };
-static StageShape stage_shape(int body, int dtype) {
-  switch (body) {
+static StageShape stage_shape(const omprt_loop_desc* d, uint64_t n) {
+  switch (d->body) {
     case OMPRT_BODY_AXPY:
-      return {2u, 4u};  // f32 or i32: x, y (y written back)
+      return {2u, 4u, 0};  // f32 or i32: x, y (y written back)
     case OMPRT_BODY_DOT:
-      return {2u, 4u};
+      return {2u, 4u, 0};
     case OMPRT_BODY_NONE:
-      if (dtype == OMPRT_F32 || dtype == OMPRT_I32) return {1u, 4u};
-      if (dtype == OMPRT_BF16) return {1u, 2u};
-      if (dtype == OMPRT_I64) return {1u, 8u};
-      return {0u, 0u};
+      if (d->data_type == OMPRT_F32 || d->data_type == OMPRT_I32) return {1u, 4u, 0};
+      if (d->data_type == OMPRT_BF16) return {1u, 2u, 0};
+      if (d->data_type == OMPRT_I64) return {1u, 8u, 0};
+      return {0u, 0u, 0};
+    case OMPRT_BODY_STENCIL1D3:  // the window is read in 16-byte units
+      return n % 4 == 0 ? StageShape{1u, 4u, 1} : StageShape{0u, 0u, 0};
+    case OMPRT_BODY_STENCIL2D5:  // and a unit must not straddle two rows
+      return n % 4 == 0 && d->nx % 4 == 0 ? StageShape{1u, 4u, (uint64_t)d->nx}
+                                          : StageShape{0u, 0u, 0};
     default:
-      return {0u, 0u};
+      return {0u, 0u, 0};
   }
 }
 
@@ -264,19 +271,46 @@ static StageShape stage_shape(int body, int dtype) {
 // work needs many warps per SM, and staging wins only with all 32 lanes busy
 // on chunks of at most 512 bytes over all arrays (dot dynamic(64) +16%, sum
 // +9%; dynamic(256) loses).
-static uint32_t stage_chunks(const omprt_ctx* c, int body, int dtype, uint64_t chunk,
-                             uint32_t threads, size_t smem_base, bool reduction) {
-  const StageShape sh = stage_shape(body, dtype);
-  if (!sh.arrays || c->stage_bytes == 0) return 0;
+struct StagePlan {
+  uint32_t chunks;      // P; 0: the plain form
+  uint32_t warp_bytes;  // shared memory per warp
+};
+static StagePlan stage_plan(const omprt_ctx* c, const StageShape& sh, uint64_t chunk,
+                            uint32_t threads, size_t smem_base, bool reduction) {
+  const StagePlan none = {0u, 0u};
+  if (!sh.arrays || c->stage_bytes == 0) return none;
   const uint64_t cb = chunk * sh.elem;
-  if (cb % 16 || cb < 256 || cb > c->stage_bytes) return 0;
-  const uint64_t warps = threads / 32;
-  uint64_t P = c->stage_bytes / warps / (sh.arrays * cb);
-  if (P > 32) P = 32;
-  if (reduction ? (P < 32 || sh.arrays * cb > 512) : P < 16) return 0;
+  if (cb % 16 || cb < 256 || cb > c->stage_bytes) return none;
+  const uint64_t warps = threads / 32, per_warp = c->stage_bytes / warps;
+  uint64_t P;
+  if (sh.halo) {
+    // window of at most P c + 2 halo + 6 elements (16-byte widened), then P
+    // chunks of output.  The halo is re-read from L2 by every pass, so it
+    // must stay small against the pass: at most a quarter of it (a 2-D grid
+    // of 4096-wide rows needs two 16 KB halo rows per pass, and measured
+    // slower staged: 0.21 against 0.25 for dynamic(256)).  A stencil unit
+    // costs an owner lane several times an axpy unit, so long chunks walked
+    // by one lane lose (1-D, n = 2^26: c = 64 0.94 staged against 0.69,
+    // c = 128 0.74 against 0.65, c = 256 0.59 against 0.68): chunks of at
+    // most 512 bytes.
+    if (reduction || cb > 512) return none;
+    const uint64_t fixed = (2 * sh.halo + 8) * sh.elem;
+    P = per_warp > fixed ? (per_warp - fixed) / (2 * cb) : 0;
+    if (P > 32) P = 32;
+    if (P == 0 || 8 * sh.halo * sh.elem > P * cb) return none;
+  } else {
+    P = per_warp / (sh.arrays * cb);
+    if (P > 32) P = 32;
+    if (reduction ? (P < 32 || sh.arrays * cb > 512) : P < 16) return none;
+  }
+  // equal passes: a claim of 32 chunks in ceil(32 / P) passes of (nearly)
+  // the same size, not P, P, ..., remainder
+  P = (32 + (32 + P - 1) / P - 1) / ((32 + P - 1) / P);
+  const uint64_t wb = sh.halo ? ((P * chunk + 2 * sh.halo + 8) * sh.elem + 15) / 16 * 16 + P * cb
+                              : P * sh.arrays * cb;
   // leave room for the kernel's static shared memory
-  if (smem_base + warps * P * sh.arrays * cb + 2048 > (uint64_t)c->max_smem_optin) return 0;
-  return (uint32_t)P;
+  if (smem_base + warps * wb + 2048 > (uint64_t)c->max_smem_optin) return none;
+  return {(uint32_t)P, (uint32_t)wb};
 }
 
 static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, int64_t dist_chunk,
@@ -371,13 +405,14 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
   if (ksched == kStatic && n % ((uint64_t)teams * (uint64_t)threads) == 0)
     stage_c = n / ((uint64_t)teams * (uint64_t)threads);
   if (stage_c) {
-    a.stage_chunks = stage_chunks(c, d->body, d->data_type, stage_c, (uint32_t)threads, smem,
-                                  acc != kAccNone);
-    if (a.stage_chunks) {
-      const StageShape sh = stage_shape(d->body, d->data_type);
+    const StagePlan sp = stage_plan(c, stage_shape(d, n), stage_c, (uint32_t)threads, smem,
+                                    acc != kAccNone);
+    if (sp.chunks) {
+      a.stage_chunks = sp.chunks;
+      a.stage_warp_bytes = sp.warp_bytes;
       a.stage_off = (uint32_t)smem;
       if (ksched == kStatic) a.chunk = stage_c;
-      smem += (size_t)(threads / 32) * a.stage_chunks * sh.arrays * (size_t)stage_c * sh.elem;
+      smem += (size_t)(threads / 32) * sp.warp_bytes;
     }
   }
   cudaStream_t st = (cudaStream_t)stream;

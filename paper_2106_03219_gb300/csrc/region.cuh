@@ -41,9 +41,9 @@ struct RegionArgs {
   uint32_t pool_bytes;   // fallback pool bytes per team
   unsigned char* pool;   // team g's slice at pool + g * pool_bytes (g < pool_teams)
   uint32_t pool_teams;
-  uint32_t stage_chunks;  // kDynamic, streaming bodies: chunks per staged pass (0: no staging)
+  uint32_t stage_chunks;  // staged schedules: chunks per pass (0: the plain form)
   uint32_t stage_off;     // byte offset of the staging buffers in dynamic shared memory
-  uint32_t pad;
+  uint32_t stage_warp_bytes;  // staging buffer bytes per warp
   unsigned char* partials;        // 16 bytes per team
   uint32_t* ticket;               // cross-team ticket (wraps to 0 by itself)
   unsigned long long* dyn_next;   // per-team dynamic dispatch counters (left 0)
@@ -422,6 +422,40 @@ struct BodyStencil1D {
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc.add(as_f(o[k]));
   }
+  // staged form: one input window (the pass and one element on each side,
+  // widened to 16-byte units) and an output buffer; needs n % 4 == 0
+  static constexpr int kStageArrays = 1;
+  static constexpr bool kStageWrites = true;
+  static constexpr bool kStageHalo = true;
+  static constexpr uint32_t kElemBytes = 4;
+  __device__ const void* stage_src(int) const { return in; }
+  __device__ void* stage_dst() const { return out; }
+  __device__ uint64_t stage_halo() const { return 1; }
+  __device__ uint64_t stage_n() const { return n; }
+  // outputs gi .. gi+3 (gi % 4 == 0) from window w, w[j] = in[gi]
+  template <class Acc>
+  __device__ __forceinline__ float4 stage_unit_halo(const float* w, uint32_t j, uint64_t gi,
+                                                    Acc& acc) const {
+    const float4 cc = *(const float4*)(w + j);
+    float4 o;
+    if (gi >= 1 && gi + 4 < n) {  // all four interior
+      const float wl = w[j - 1], er = w[j + 4];
+      o.x = point(wl, cc.x, cc.y);
+      o.y = point(cc.x, cc.y, cc.z);
+      o.z = point(cc.y, cc.z, cc.w);
+      o.w = point(cc.z, cc.w, er);
+    } else {  // an end point among them: copied; its neighbours are not read
+      o.x = gi == 0 || gi + 1 == n ? cc.x : point(w[j - 1], cc.x, cc.y);
+      o.y = gi + 2 == n ? cc.y : point(cc.x, cc.y, cc.z);
+      o.z = gi + 3 == n ? cc.z : point(cc.y, cc.z, cc.w);
+      o.w = gi + 4 == n ? cc.w : point(cc.z, cc.w, w[j + 4]);
+    }
+    acc.add(o.x);
+    acc.add(o.y);
+    acc.add(o.z);
+    acc.add(o.w);
+    return o;
+  }
 };
 
 // 2-D 5-point stencil on ny x nx row-major, out of place; boundary copied.
@@ -497,6 +531,40 @@ struct BodyStencil2D {
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc.add(as_f(o[k]));
   }
+  // staged form: one input window (the pass and one row on each side,
+  // widened to 16-byte units) and an output buffer; needs nx % 4 == 0, so a
+  // 16-byte unit never straddles two rows
+  static constexpr int kStageArrays = 1;
+  static constexpr bool kStageWrites = true;
+  static constexpr bool kStageHalo = true;
+  static constexpr uint32_t kElemBytes = 4;
+  __device__ const void* stage_src(int) const { return in; }
+  __device__ void* stage_dst() const { return out; }
+  __device__ uint64_t stage_halo() const { return nx; }
+  __device__ uint64_t stage_n() const { return nx * ny; }
+  // outputs gi .. gi+3 (gi % 4 == 0, so in one row, first column c % 4 == 0)
+  // from window w, w[j] = in[gi].  Of the four, only column 0 (first) and
+  // column nx - 1 (last) can be boundary columns.
+  template <class Acc>
+  __device__ __forceinline__ float4 stage_unit_halo(const float* w, uint32_t j, uint64_t gi,
+                                                    Acc& acc) const {
+    const float4 cc = *(const float4*)(w + j);
+    const uint64_t r = row_of(gi), c = gi - r * nx;
+    float4 o = cc;  // boundary rows are copied
+    if (r >= 1 && r + 1 < ny) {
+      const float4 nn = *(const float4*)(w + j - nx);
+      const float4 ss = *(const float4*)(w + j + nx);
+      o.x = c > 0 ? point(nn.x, ss.x, cc.y, w[j - 1], cc.x) : cc.x;
+      o.y = point(nn.y, ss.y, cc.z, cc.x, cc.y);
+      o.z = point(nn.z, ss.z, cc.w, cc.y, cc.z);
+      o.w = c + 4 < nx ? point(nn.w, ss.w, w[j + 4], cc.z, cc.w) : cc.w;
+    }
+    acc.add(o.x);
+    acc.add(o.y);
+    acc.add(o.z);
+    acc.add(o.w);
+    return o;
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -524,15 +592,28 @@ __device__ __forceinline__ void run_one(const Body& b, uint64_t i, Acc& acc) {
 #ifndef OMPRT_WIDE_SCALAR_GROUP
 #define OMPRT_WIDE_SCALAR_GROUP 2
 #endif
+#ifndef OMPRT_SCALAR_GROUP
+#define OMPRT_SCALAR_GROUP 4
+#endif
+// static(1): each thread's iterations are a stride-T scalar sequence, the
+// whole loop for that thread, so deeper groups pay (axpy at n = 2^26: 1.00 of
+// the copy rate with 8, 0.92 with 4, 0.985 with 16); elsewhere the scalar
+// path is a head or tail and 8 only costs registers (spills in dist).
+#ifndef OMPRT_STRIDED_GROUP
+#define OMPRT_STRIDED_GROUP 8
+#endif
 template <class Body>
 struct ScalarGroup {
-  static constexpr int value = InFlight<Body>::value >= 2 ? 4 : OMPRT_WIDE_SCALAR_GROUP;
+  static constexpr int value = InFlight<Body>::value >= 2 ? OMPRT_SCALAR_GROUP : OMPRT_WIDE_SCALAR_GROUP;
+};
+template <class Body>
+struct StridedGroup {
+  static constexpr int value = InFlight<Body>::value >= 2 ? OMPRT_STRIDED_GROUP : OMPRT_WIDE_SCALAR_GROUP;
 };
 
-template <class Body, class Acc>
+template <class Body, class Acc, int kU = ScalarGroup<Body>::value>
 __device__ __forceinline__ void run_scalar(const Body& b, uint64_t base, uint64_t step,
                                            uint64_t cnt, Acc& acc) {
-  constexpr int kU = ScalarGroup<Body>::value;
   uint64_t k = 0;
   for (; k + kU <= cnt; k += kU) {
     typename Body::S1 s[kU];
@@ -578,7 +659,8 @@ __device__ __forceinline__ void run_range(const Body& b, uint64_t a, uint64_t e,
 template <class Body, class Acc>
 __device__ __forceinline__ void run_strided(const Body& b, uint64_t base, uint64_t cnt, uint32_t t,
                                             uint32_t T, Acc& acc) {
-  if (t < cnt) run_scalar(b, base + t, T, (cnt - t + T - 1) / T, acc);
+  if (t < cnt)
+    run_scalar<Body, Acc, StridedGroup<Body>::value>(b, base + t, T, (cnt - t + T - 1) / T, acc);
 }
 
 // schedule(auto): 32-byte vectors grid-stride over the whole loop.
@@ -901,6 +983,12 @@ template <class Body, class = void>
 struct Stageable : std::false_type {};
 template <class Body>
 struct Stageable<Body, std::void_t<decltype(Body::kStageArrays)>> : std::true_type {};
+// bodies that read neighbours (the stencils): the pass's input window
+// reaches stage_halo() elements beyond it on both sides
+template <class Body, class = void>
+struct StageHalo : std::false_type {};
+template <class Body>
+struct StageHalo<Body, std::void_t<decltype(Body::kStageHalo)>> : std::true_type {};
 
 static __shared__ __align__(8) uint64_t rt_stage_bar[OMPRT_MAX_THREADS / 32];
 constexpr uint64_t kStageWaitNs = 1000000000ull;  // 1 s: a pass takes microseconds
@@ -912,6 +1000,7 @@ __device__ __forceinline__ bool stage_ok(const Body& b, uint64_t bs) {
   uintptr_t m = (uintptr_t)(bs * Body::kElemBytes);
 #pragma unroll
   for (int k = 0; k < Body::kStageArrays; ++k) m |= (uintptr_t)b.stage_src(k);
+  if constexpr (Body::kStageWrites) m |= (uintptr_t)b.stage_dst();
   return (m & 15) == 0;
 }
 
@@ -945,8 +1034,12 @@ __device__ void run_staged(const Body& b, const RegionArgs& a, uint64_t bs, uint
   const uint32_t uc = cb / 16;             // units per chunk
   const uint64_t nch = bn ? (bn - 1) / c + 1 : 0;
   const uint32_t lane = lane_id(), w = warp_id();
-  const size_t array_bytes = (size_t)P * cb;  // array k at buf + k * array_bytes
-  unsigned char* const buf = rt_dyn_smem + a.stage_off + (size_t)w * A * array_bytes;
+  constexpr bool kHalo = StageHalo<Body>::value;
+  // streaming bodies: array k at buf + k * array_bytes.  Halo bodies: the
+  // input window at buf, the output buffer at the end of the warp's bytes.
+  const size_t array_bytes = (size_t)P * cb;
+  unsigned char* const buf = rt_dyn_smem + a.stage_off + (size_t)w * a.stage_warp_bytes;
+  unsigned char* const outb = buf + a.stage_warp_bytes - array_bytes;
   const uint32_t bar = smem_addr(&rt_stage_bar[w]);
   if (lane == 0) mbar_init(bar);
   __syncwarp();
@@ -962,15 +1055,28 @@ __device__ void run_staged(const Body& b, const RegionArgs& a, uint64_t bs, uint
       const uint64_t E = (base + p0 + np) * c < bn ? (base + p0 + np) * c : bn;
       const uint32_t units = (uint32_t)((E - S) / EPU);
       const uint32_t bytes = units * 16;
+      uint64_t wS = 0;  // halo bodies: the window is in[wS, wE)
       if (bytes) {
         bool ok = true;
-        if (lane == 0) {
+        if constexpr (kHalo) {
+          const uint64_t h = b.stage_halo(), nn = b.stage_n();  // nn % 4 == 0 (host check)
+          wS = (bs + S > h ? bs + S - h : 0) & ~3ull;
+          const uint64_t wE = ((bs + E + h < nn ? bs + E + h : nn) + 3) & ~3ull;
+          if (lane == 0) {
+            bulk_wait_read();  // the last store has read the output buffer
+            const uint32_t wbytes = (uint32_t)((wE - wS) * 4);
+            mbar_expect_tx(bar, wbytes);
+            bulk_g2s(buf, (const float*)b.stage_src(0) + wS, wbytes, bar);
+          }
+        } else if (lane == 0) {
           if constexpr (Body::kStageWrites) bulk_wait_read();  // last store has read the buffer
           mbar_expect_tx(bar, A * bytes);
 #pragma unroll
           for (int k = 0; k < A; ++k)
             bulk_g2s(buf + k * array_bytes, (const char*)b.stage_src(k) + (bs + S) * EB, bytes,
                      bar);
+        }
+        if (lane == 0) {
           // lane 0 waits (suspended, not spinning); the others block in the
           // warp barrier, which also orders their reads after lane 0's wait
           ok = mbar_wait(bar, phase, kStageWaitNs, a.status);
@@ -995,11 +1101,18 @@ __device__ void run_staged(const Body& b, const RegionArgs& a, uint64_t bs, uint
           for (uint32_t q0 = 0; q0 < nu; ++q0) {
             uint32_t q = q0 + off;
             if (q >= nu) q -= nu;
-            uint4 u[A];
+            if constexpr (kHalo) {
+              const uint64_t gi = bs + S + (uint64_t)(u0 + q) * 4;
+              ((float4*)outb)[u0 + q] =
+                  b.stage_unit_halo((const float*)buf, (uint32_t)(gi - wS), gi, acc);
+            } else {
+              uint4 u[A];
 #pragma unroll
-            for (int k = 0; k < A; ++k) u[k] = ((const uint4*)(buf + k * array_bytes))[u0 + q];
-            b.stage_unit(u, acc);
-            if constexpr (Body::kStageWrites) ((uint4*)(buf + (A - 1) * array_bytes))[u0 + q] = u[A - 1];
+              for (int k = 0; k < A; ++k) u[k] = ((const uint4*)(buf + k * array_bytes))[u0 + q];
+              b.stage_unit(u, acc);
+              if constexpr (Body::kStageWrites)
+                ((uint4*)(buf + (A - 1) * array_bytes))[u0 + q] = u[A - 1];
+            }
           }
         }
         const uint64_t t0 = lo > vend ? lo : vend;
@@ -1009,7 +1122,8 @@ __device__ void run_staged(const Body& b, const RegionArgs& a, uint64_t bs, uint
       __syncwarp();
       if constexpr (Body::kStageWrites) {
         if (lane == 0 && bytes)
-          bulk_s2g((char*)b.stage_dst() + (bs + S) * EB, buf + (A - 1) * array_bytes, bytes);
+          bulk_s2g((char*)b.stage_dst() + (bs + S) * EB, kHalo ? outb : buf + (A - 1) * array_bytes,
+                   bytes);
       }
     }
   }

@@ -194,3 +194,66 @@ def test_stage_bytes_validation(rt):
     with pytest.raises(R.OmprtError):
         rt.set_stage_bytes(1 << 30)
     rt.set_stage_bytes(DEFAULT_STAGE)
+
+
+# -- stencils: the pass's input window (one row / one element on each side)
+# is staged with one bulk copy; outputs go back by one bulk store per pass.
+
+STENCIL_SCHEDS = [(R.SCHED_DYNAMIC, 64), (R.SCHED_DYNAMIC, 256), (R.SCHED_STATIC_CHUNKED, 64),
+                  (R.SCHED_STATIC_CHUNKED, 68), (R.SCHED_STATIC, 0)]
+
+
+@pytest.mark.parametrize("sched,chunk", STENCIL_SCHEDS)
+@pytest.mark.parametrize("ny,nx", [(64, 64), (67, 40), (4, 4), (9, 8), (130, 516), (33, 1028),
+                                   (65, 42), (256, 256)])
+@pytest.mark.parametrize("budget", [32768, 131072])
+def test_stencil2d_staged_bit_exact(staged, sched, chunk, ny, nx, budget):
+    """nx % 4 != 0 (42) runs the plain form."""
+    import torch
+    rt = staged
+    rt.set_stage_bytes(budget)
+    a = inputs.grid_f32(ny, nx, 6)
+    ad = dev(a)
+    want = bits32(O.stencil2d5(a))
+    for G, T in ((1, 32), (3, 64), (16, 32), (64, 128)):
+        out = torch.full((ny, nx), -7.0, device="cuda")
+        rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=ny * nx, x=ad, out=out, nx=nx, ny=ny),
+                         sched, chunk, G, T)
+        assert np.array_equal(bits32(host(out)), want), (G, T)
+    assert rt.sync_status() == 0
+
+
+@pytest.mark.parametrize("sched,chunk", STENCIL_SCHEDS)
+@pytest.mark.parametrize("n", [4, 4096, 4100, 65536, 300000, 300001])
+def test_stencil1d_staged_bit_exact(staged, sched, chunk, n):
+    """n % 4 != 0 (300001) runs the plain form."""
+    import torch
+    rt = staged
+    a = inputs.f32_uniform01(n, 4)
+    ad = dev(a)
+    want = bits32(O.stencil1d3(a))
+    for G, T in ((1, 32), (7, 64), (64, 32)):
+        out = torch.full((n,), -7.0, device="cuda")
+        rt.launch_region(R.loop_desc(R.BODY_STENCIL1D3, n=n, x=ad, out=out), sched, chunk, G, T)
+        assert np.array_equal(bits32(host(out)), want), (G, T)
+    assert rt.sync_status() == 0
+
+
+def test_stencil2d_staged_full_grid(staged):
+    """The 4096 x 4096 grid of the worksharing sweep under large budgets: a
+    pass would need two 16 KB halo rows, more than a quarter of the pass, so
+    the host runs the plain form; results must not depend on the budget."""
+    import torch
+    rt = staged
+    a = inputs.grid_f32(4096, 4096, 0)
+    ad = dev(a)
+    want = bits32(O.stencil2d5(a))
+    for budget in (65536, 196608):
+        rt.set_stage_bytes(budget)
+        for sched, chunk, G, T in ((R.SCHED_DYNAMIC, 256, 4096, 32), (R.SCHED_STATIC_CHUNKED, 64,
+                                   2048, 64), (R.SCHED_STATIC, 0, 4096, 32)):
+            out = torch.empty_like(ad)
+            rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=4096 * 4096, x=ad, out=out, nx=4096,
+                                         ny=4096), sched, chunk, G, T)
+            assert np.array_equal(bits32(host(out)), want), (budget, sched, G, T)
+    assert rt.sync_status() == 0
