@@ -597,10 +597,14 @@ __device__ __forceinline__ void run_one(const Body& b, uint64_t i, Acc& acc) {
 #endif
 // static(1): each thread's iterations are a stride-T scalar sequence, the
 // whole loop for that thread, so deeper groups pay (axpy at n = 2^26: 1.00 of
-// the copy rate with 8, 0.92 with 4, 0.985 with 16); elsewhere the scalar
-// path is a head or tail and 8 only costs registers (spills in dist).
+// the copy rate with 8, 0.92 with 4, 0.985 with 16; the 4096^2 2-D stencil:
+// 0.38 with 4, 0.33 with 2, 0.31 with 8); elsewhere the scalar path is a head
+// or tail and deeper groups only cost registers (spills in dist).
 #ifndef OMPRT_STRIDED_GROUP
 #define OMPRT_STRIDED_GROUP 8
+#endif
+#ifndef OMPRT_WIDE_STRIDED_GROUP
+#define OMPRT_WIDE_STRIDED_GROUP 4
 #endif
 template <class Body>
 struct ScalarGroup {
@@ -608,7 +612,7 @@ struct ScalarGroup {
 };
 template <class Body>
 struct StridedGroup {
-  static constexpr int value = InFlight<Body>::value >= 2 ? OMPRT_STRIDED_GROUP : OMPRT_WIDE_SCALAR_GROUP;
+  static constexpr int value = InFlight<Body>::value >= 2 ? OMPRT_STRIDED_GROUP : OMPRT_WIDE_STRIDED_GROUP;
 };
 
 template <class Body, class Acc, int kU = ScalarGroup<Body>::value>
