@@ -417,6 +417,14 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
+  if (d->body == OMPRT_BODY_STENCIL2D5 && ksched == kAuto && acc == kAccNone &&
+      d->data_type == OMPRT_F32) {
+    e = launch_stencil2d_tiles(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny,
+                               (float)d->c0, (float)d->c1, (unsigned)teams, (unsigned)threads,
+                               c->status_dev, st);
+    if (e != cudaErrorNotSupported) return from_cuda(e);
+    cudaGetLastError();
+  }
   const bool f32path = d->data_type == OMPRT_F32 || d->data_type == OMPRT_BF16;
   if (d->body == OMPRT_BODY_MAP_RECORD || !f32path)
     e = launch_region_int(d->body, d->data_type, acc, ksched, (unsigned)teams, (unsigned)threads,

@@ -34,6 +34,12 @@ cudaError_t launch_stencil(int body, int acc, int sched, unsigned grid, unsigned
 cudaError_t launch_dot_load(int body, int dtype, int acc, int sched, unsigned grid,
                             unsigned block, size_t smem, cudaStream_t st, const RegionArgs& a);
 
+// schedule(auto) 2-D stencil on tensor tiles (k_stencil_tiles.cu);
+// cudaErrorNotSupported (nothing launched) where that form does not apply.
+cudaError_t launch_stencil2d_tiles(const void* in, float* out, uint64_t nx, uint64_t ny, float c0,
+                                   float c1, unsigned teams, unsigned threads, uint32_t* status,
+                                   cudaStream_t st);
+
 // Support kernels (k_support.cu).
 cudaError_t launch_static_table(uint64_t n, int64_t lb, int64_t incr, uint64_t chunk, unsigned G,
                                 unsigned T, int64_t* table, cudaStream_t st);

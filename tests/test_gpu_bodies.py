@@ -119,3 +119,52 @@ def test_axpy_full_size_static(rt):
     rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0), R.SCHED_STATIC, 0,
                      592, 256)
     assert np.array_equal(bits32(host(yd)), bits32(O.axpy_f32(3.0, x, y)))
+
+
+@pytest.mark.parametrize("ny,nx", [(1, 4), (2, 8), (4, 4), (9, 8), (33, 132), (100, 260),
+                                   (67, 40), (31, 4), (1024, 1024)])
+@pytest.mark.parametrize("G,T", [(1, 32), (5, 64), (37, 96), (152, 128), (4096, 256),
+                                 (64, 1024)])
+def test_stencil2d_auto_tiles_bit_exact(rt, ny, nx, G, T):
+    """schedule(auto) runs the 2-D stencil on tensor-copied tiles of 128 x 32
+    when nx % 4 == 0: bit-exact at ragged tile edges, for 1, 2, 4 and 8 warps
+    per team and more teams than tiles."""
+    import torch
+    a = inputs.grid_f32(ny, nx, 6)
+    ad = dev(a)
+    out = torch.full((ny, nx), -7.0, device="cuda")
+    rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=ny * nx, x=ad, out=out, nx=nx, ny=ny),
+                     R.SCHED_AUTO, 0, G, T)
+    assert np.array_equal(bits32(host(out)), bits32(O.stencil2d5(a)))
+    assert rt.sync_status() == 0
+
+
+def test_stencil2d_auto_fallbacks(rt):
+    """Misaligned output, nx % 4 != 0 and a reduction run the strip-walking
+    form; all bit-exact (the reduction within the sum bound)."""
+    import torch
+    from gpu_helpers import fp_sum_ok
+    ny, nx = 70, 136
+    a = inputs.grid_f32(ny, nx, 6)
+    ad = dev(a)
+    want = O.stencil2d5(a)
+    buf = torch.full((ny * nx + 1,), -7.0, device="cuda")
+    out = buf[1:]  # 4-byte aligned only
+    rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=ny * nx, x=ad, out=out, nx=nx, ny=ny),
+                     R.SCHED_AUTO, 0, 17, 128)
+    assert np.array_equal(bits32(host(out)), bits32(want.reshape(-1)))
+    b = inputs.grid_f32(9, 10, 7)
+    outb = torch.full((9, 10), -7.0, device="cuda")
+    rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=90, x=dev(b), out=outb, nx=10, ny=9),
+                     R.SCHED_AUTO, 0, 3, 64)
+    assert np.array_equal(bits32(host(outb)), bits32(O.stencil2d5(b)))
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out2 = torch.full((ny, nx), -7.0, device="cuda")
+    rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=ny * nx, x=ad, out=out2, nx=nx, ny=ny),
+                     R.SCHED_AUTO, 0, 17, 128,
+                     red=R.ReduceDesc(R.OP_SUM, R.PREC_COMP_F64, res.data_ptr()))
+    assert np.array_equal(bits32(host(out2)), bits32(want))
+    ok, err, bound = fp_sum_ok(float(host(res)[0]), O.exact_sum_f32(want.reshape(-1)),
+                               O.exact_abs_sum_f32(want.reshape(-1)))
+    assert ok, (err, bound)
+    assert rt.sync_status() == 0
