@@ -21,6 +21,10 @@ enum : int { kStatic = 0, kChunked = 1, kDynamic = 2, kAuto = 3, kDist = 4, kGui
 #ifndef OMPRT_MAX_THREADS
 #define OMPRT_MAX_THREADS 1024
 #endif
+// Vectors each thread keeps in flight in the value bodies of reductions.
+#ifndef OMPRT_LOAD_INFLIGHT
+#define OMPRT_LOAD_INFLIGHT 2
+#endif
 
 // Everything a region kernel needs, passed by value (one parameter block).
 struct RegionArgs {
@@ -234,6 +238,7 @@ struct BodyDotF32 {
 struct BodyLoadF32 {
   static constexpr bool kVec = true;
   static constexpr int VEC = 8;
+  static constexpr int kInFlight = OMPRT_LOAD_INFLIGHT;
   struct Frag { uint32_t x[8]; };
   const float* x;
   __device__ explicit BodyLoadF32(const RegionArgs& r) : x((const float*)r.x) {}
@@ -267,6 +272,7 @@ struct BodyLoadF32 {
 struct BodyLoadBF16 {
   static constexpr bool kVec = true;
   static constexpr int VEC = 16;
+  static constexpr int kInFlight = OMPRT_LOAD_INFLIGHT;
   struct Frag { uint32_t x[8]; };
   const uint16_t* x;
   __device__ explicit BodyLoadBF16(const RegionArgs& r) : x((const uint16_t*)r.x) {}
@@ -306,6 +312,7 @@ struct BodyLoadBF16 {
 struct BodyLoadI32 {
   static constexpr bool kVec = true;
   static constexpr int VEC = 8;
+  static constexpr int kInFlight = OMPRT_LOAD_INFLIGHT;
   struct Frag { uint32_t x[8]; };
   const int32_t* x;
   __device__ explicit BodyLoadI32(const RegionArgs& r) : x((const int32_t*)r.x) {}
@@ -338,6 +345,7 @@ struct BodyLoadI32 {
 struct BodyLoadI64 {
   static constexpr bool kVec = true;
   static constexpr int VEC = 4;
+  static constexpr int kInFlight = OMPRT_LOAD_INFLIGHT;
   struct Frag { uint64_t x[4]; };
   const int64_t* x;
   __device__ explicit BodyLoadI64(const RegionArgs& r) : x((const int64_t*)r.x) {}

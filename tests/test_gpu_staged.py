@@ -257,3 +257,44 @@ def test_stencil2d_staged_full_grid(staged):
                                          ny=4096), sched, chunk, G, T)
             assert np.array_equal(bits32(host(out)), want), (budget, sched, G, T)
     assert rt.sync_status() == 0
+
+
+def test_staged_and_tiled_forms_in_a_cuda_graph(staged):
+    """Staged dynamic / static launches, a staged 1-D stencil and the
+    tensor-tiled 2-D stencil (its tensor map is a kernel parameter) captured
+    in one CUDA graph: every replay reproduces the eager results bit for bit."""
+    import torch
+    rt = staged
+    n = (1 << 20) + 12
+    x = inputs.f32_uniform01(n, 0)
+    y0 = inputs.f32_uniform01(n, 1)
+    xd, yd = dev(x), dev(y0)
+    a1 = inputs.f32_uniform01(1 << 20, 4)
+    a1d = dev(a1)
+    o1 = torch.empty_like(a1d)
+    g2 = inputs.grid_f32(1000, 1028, 6)
+    g2d = dev(g2)
+    o2 = torch.empty_like(g2d)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        d = R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0)
+        rt.launch_region(d, R.SCHED_DYNAMIC, 256, 64, 32, stream=s)
+        rt.launch_region(d, R.SCHED_STATIC_CHUNKED, 64, 16, 128, stream=s)
+        rt.launch_region(R.loop_desc(R.BODY_STENCIL1D3, n=1 << 20, x=a1d, out=o1),
+                         R.SCHED_DYNAMIC, 64, 64, 32, stream=s)
+        rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=1000 * 1028, x=g2d, out=o2, nx=1028,
+                                     ny=1000), R.SCHED_AUTO, 0, 152, 256, stream=s)
+    want_y = O.axpy_f32(3.0, x, O.axpy_f32(3.0, x, y0))
+    for _ in range(3):
+        yd.copy_(dev(y0))
+        o1.fill_(-7.0)
+        o2.fill_(-7.0)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(bits32(host(yd)), bits32(want_y))
+        assert np.array_equal(bits32(host(o1)), bits32(O.stencil1d3(a1)))
+        assert np.array_equal(bits32(host(o2)), bits32(O.stencil2d5(g2)))
+    assert rt.sync_status() == 0
