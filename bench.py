@@ -253,7 +253,8 @@ def main():
                     help="skip the reduction and batched-region measurements")
     ap.add_argument("--single", default=None,
                     help="profiling aid: only launch plan entries whose name contains this "
-                         "(e.g. axpy/auto), warmup + steps times, and print their mean time")
+                         "(e.g. axpy/auto), or one of reduce/fp32, reduce/bf16, reduce/int64, "
+                         "batch; warmup + steps times, and print the mean time")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -291,6 +292,9 @@ def main():
         return L
 
     plan = launches(x, y, grid, out)
+    if args.single and (args.single.startswith("reduce/") or args.single == "batch"):
+        del x, y, grid, out, plan
+        return run_single_extra(rt, R, torch, inputs, args)
     if args.single:
         return run_single(rt, torch, plan, args)
     step_bytes = sum(b for _, b, *_ in plan)
@@ -373,6 +377,51 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def run_single_extra(rt, R, torch, inputs, args):
+    """--single reduce/{fp32,bf16,int64}: the reduction of the bench's
+    reductions leg (n = 2^28, 4 teams per SM x 512 threads); --single batch:
+    one persistent launch over the 4096-region batch."""
+    import numpy as np
+    stream = torch.cuda.current_stream()
+    if args.single == "batch":
+        from paper_2106_03219_gb300 import batched
+        from paper_2106_03219_gb300.autotune import load_batch_table
+        chunk, threads = load_batch_table()
+        rs = batched.RegionSet()
+        b = rs.batch(rt, chunk)
+        fn = lambda: b.launch(0, threads, stream=stream)
+        nbytes = rs.algorithmic_bytes()
+    else:
+        n = 1 << 28
+        gen = {"reduce/fp32": lambda: inputs.f32_uniform_pm1(n, 0),
+               "reduce/bf16": lambda: inputs.bf16_uniform_pm1(n, 0).view(np.int16),
+               "reduce/int64": lambda: inputs.int64_uniform(n, 0)}.get(args.single)
+        if gen is None:
+            raise SystemExit("unknown --single %r" % args.single)
+        t = torch.from_numpy(gen()).cuda()
+        if args.single == "reduce/bf16":
+            t = t.view(torch.bfloat16)
+        r = torch.zeros(1, dtype=torch.int64 if args.single == "reduce/int64" else torch.float64,
+                        device="cuda")
+        sms = rt.sm_count
+        fn = lambda: rt.reduce(R.OP_SUM, t, r, R.PREC_COMP_F64, 4 * sms, 512, stream=stream)
+        nbytes = t.numel() * t.element_size()
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert rt.sync_status() == 0
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"single": args.single, "ms": ms, "GBps": nbytes / (ms * 1e-3) / 1e9}))
+    rt.close()
     return 0
 
 

@@ -119,7 +119,7 @@ struct BodyAxpyF32 {
     for (int k = 0; k < 8; ++k) f.y[k] = as_u(__fmaf_rn(a, as_f(f.x[k]), as_f(f.y[k])));
     st8<kN>(y + i, f.y);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc.add(as_f(f.y[k]));
+    for (int k = 0; k < 8; k += 2) acc_add2(acc, as_f(f.y[k]), as_f(f.y[k + 1]));
   }
   // staged dynamic path: x and y through shared memory, y written back
   static constexpr int kStageArrays = 2;
@@ -133,10 +133,8 @@ struct BodyAxpyF32 {
     u[1].y = as_u(__fmaf_rn(a, as_f(u[0].y), as_f(u[1].y)));
     u[1].z = as_u(__fmaf_rn(a, as_f(u[0].z), as_f(u[1].z)));
     u[1].w = as_u(__fmaf_rn(a, as_f(u[0].w), as_f(u[1].w)));
-    acc.add(as_f(u[1].x));
-    acc.add(as_f(u[1].y));
-    acc.add(as_f(u[1].z));
-    acc.add(as_f(u[1].w));
+    acc_add2(acc, as_f(u[1].x), as_f(u[1].y));
+    acc_add2(acc, as_f(u[1].z), as_f(u[1].w));
   }
 };
 
@@ -218,7 +216,9 @@ struct BodyDotF32 {
   template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc.add(__fmul_rn(as_f(f.x[k]), as_f(f.y[k])));
+    for (int k = 0; k < 8; k += 2)
+      acc_add2(acc, __fmul_rn(as_f(f.x[k]), as_f(f.y[k])),
+               __fmul_rn(as_f(f.x[k + 1]), as_f(f.y[k + 1])));
   }
   static constexpr int kStageArrays = 2;
   static constexpr bool kStageWrites = false;
@@ -227,10 +227,8 @@ struct BodyDotF32 {
   __device__ void* stage_dst() const { return nullptr; }
   template <class Acc>
   __device__ __forceinline__ void stage_unit(uint4 (&u)[2], Acc& acc) const {
-    acc.add(__fmul_rn(as_f(u[0].x), as_f(u[1].x)));
-    acc.add(__fmul_rn(as_f(u[0].y), as_f(u[1].y)));
-    acc.add(__fmul_rn(as_f(u[0].z), as_f(u[1].z)));
-    acc.add(__fmul_rn(as_f(u[0].w), as_f(u[1].w)));
+    acc_add2(acc, __fmul_rn(as_f(u[0].x), as_f(u[1].x)), __fmul_rn(as_f(u[0].y), as_f(u[1].y)));
+    acc_add2(acc, __fmul_rn(as_f(u[0].z), as_f(u[1].z)), __fmul_rn(as_f(u[0].w), as_f(u[1].w)));
   }
 };
 
@@ -252,7 +250,7 @@ struct BodyLoadF32 {
   template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc.add(as_f(f.x[k]));
+    for (int k = 0; k < 8; k += 2) acc_add2(acc, as_f(f.x[k]), as_f(f.x[k + 1]));
   }
   static constexpr int kStageArrays = 1;
   static constexpr bool kStageWrites = false;
@@ -261,10 +259,8 @@ struct BodyLoadF32 {
   __device__ void* stage_dst() const { return nullptr; }
   template <class Acc>
   __device__ __forceinline__ void stage_unit(uint4 (&u)[1], Acc& acc) const {
-    acc.add(as_f(u[0].x));
-    acc.add(as_f(u[0].y));
-    acc.add(as_f(u[0].z));
-    acc.add(as_f(u[0].w));
+    acc_add2(acc, as_f(u[0].x), as_f(u[0].y));
+    acc_add2(acc, as_f(u[0].z), as_f(u[0].w));
   }
 };
 
@@ -288,10 +284,8 @@ struct BodyLoadBF16 {
   template <class Acc, bool kN = false>
   __device__ __forceinline__ void finish(uint64_t, Frag& f, Acc& acc) const {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      acc.add(as_f(f.x[k] << 16));           // element 2k (low half)
-      acc.add(as_f(f.x[k] & 0xffff0000u));   // element 2k+1 (high half)
-    }
+    for (int k = 0; k < 8; ++k)  // elements 2k (low half) and 2k+1 (high half)
+      acc_add2(acc, as_f(f.x[k] << 16), as_f(f.x[k] & 0xffff0000u));
   }
   static constexpr int kStageArrays = 1;
   static constexpr bool kStageWrites = false;
@@ -302,10 +296,7 @@ struct BodyLoadBF16 {
   __device__ __forceinline__ void stage_unit(uint4 (&u)[1], Acc& acc) const {
     const uint32_t w[4] = {u[0].x, u[0].y, u[0].z, u[0].w};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      acc.add(as_f(w[k] << 16));
-      acc.add(as_f(w[k] & 0xffff0000u));
-    }
+    for (int k = 0; k < 4; ++k) acc_add2(acc, as_f(w[k] << 16), as_f(w[k] & 0xffff0000u));
   }
 };
 

@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "omprt.h"
@@ -417,19 +418,61 @@ struct AccExtI64 {
   }
 };
 
+// Two fp32 lanes in one 64-bit register, for the packed fp32x2 arithmetic of
+// sm_100+ (each lane rounded to nearest like the scalar instruction).
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ uint64_t add2_rn(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 // Compensated fp32 sum: running (s, c) with s + c the sum so far; every add
-// is an exact TwoSum whose rounding error is collected in c.
+// is an exact TwoSum whose rounding error is collected in c.  Two such sums
+// run interleaved, one per lane of a packed fp32x2 register: add2 feeds a
+// pair of values to both with one packed TwoSum (half the instructions of two
+// scalar ones); add feeds the first.  part() joins them with one more TwoSum.
 struct AccCompF32 {
   static constexpr bool kActive = true;
+  static constexpr bool kPacked = true;
   using Part = float2;  // (s, c)
-  float s = 0.f, c = 0.f;
+  uint64_t s2 = 0, c2 = 0;  // lanes (s0, s1) and (c0, c1); all-zero bits are (0.f, 0.f)
   __device__ __forceinline__ void add(float v) {
+    float2 s = unpack2(s2), c = unpack2(c2);
     float t, e;
-    two_sum(s, v, t, e);
-    s = t;
-    c = __fadd_rn(c, e);
+    two_sum(s.x, v, t, e);
+    s2 = pack2(t, s.y);
+    c2 = pack2(__fadd_rn(c.x, e), c.y);
   }
-  __device__ __forceinline__ Part part() const { return make_float2(s, c); }
+  __device__ __forceinline__ void add2(float a, float b) {
+    const uint64_t v = pack2(a, b);
+    const uint64_t t = add2_rn(s2, v);  // TwoSum, lane by lane
+    const uint64_t bp = sub2(t, s2);
+    const uint64_t ap = sub2(t, bp);
+    const uint64_t e = add2_rn(sub2(s2, ap), sub2(v, bp));
+    s2 = t;
+    c2 = add2_rn(c2, e);
+  }
+  __device__ __forceinline__ Part part() const {
+    const float2 s = unpack2(s2), c = unpack2(c2);
+    float t, e;
+    two_sum(s.x, s.y, t, e);
+    return make_float2(t, __fadd_rn(__fadd_rn(c.x, c.y), e));
+  }
   __device__ static __forceinline__ Part identity() { return make_float2(0.f, 0.f); }
   __device__ static __forceinline__ Part merge(Part a, Part b) {
     float t, e;
@@ -440,6 +483,18 @@ struct AccCompF32 {
     return make_float2(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
   }
 };
+
+// Feed a, b (in this order) to an accumulator: packed where it has a pair
+// form, else two adds.
+template <class Acc>
+__device__ __forceinline__ void acc_add2(Acc& acc, float a, float b) {
+  if constexpr (std::is_same<Acc, AccCompF32>::value) {
+    acc.add2(a, b);
+  } else {
+    acc.add(a);
+    acc.add(b);
+  }
+}
 
 struct AccNaiveF32 {
   static constexpr bool kActive = true;
