@@ -81,12 +81,20 @@ typedef enum {
     OMPRT_SCHED_LEARNED = 4,        /* schedule, chunk and teams chosen by the
                                        context's cost model (see
                                        omprt_set_cost_model), else the heuristic */
-    OMPRT_SCHED_GUIDED = 5          /* each request takes max(c, ceil(r / 2T)) of
+    OMPRT_SCHED_GUIDED = 5,         /* each request takes max(c, ceil(r / 2T)) of
                                        the r iterations of the team's block not yet
                                        handed out (chunk c, 0 = 1); a warp claims 32
                                        such chunks with one compare-and-swap on a
                                        per-team counter (bounded retries; giving up
                                        sets OMPRT_DEV_TIMEOUT) */
+    OMPRT_SCHED_NONMONOTONIC = 6    /* schedule(nonmonotonic: dynamic, c): chunks of
+                                       c handed out at run time in any order.  The
+                                       team's groups of 32 chunks are split evenly
+                                       among its warps; a warp claims its own groups
+                                       first (a counter in shared memory), then
+                                       takes groups left to other warps.  Lane l of
+                                       a claim runs chunk 32 g + l in full; a
+                                       thread's chunks need not increase */
 } omprt_sched;
 
 typedef enum {

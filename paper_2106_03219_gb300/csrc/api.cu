@@ -355,6 +355,10 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
       break;
     case OMPRT_SCHED_AUTO: ksched = kAuto; break;
     case OMPRT_SCHED_GUIDED: ksched = kGuided; break;
+    case OMPRT_SCHED_NONMONOTONIC:
+      if (chunk < 1) return OMPRT_ERR_INVALID;
+      ksched = kNonmono;
+      break;
     default: return OMPRT_ERR_INVALID;
   }
   if (threads == 0) threads = 256;
@@ -401,7 +405,7 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
   // lanes own (static without chunk: one block of n / (G T) per thread, used
   // only when that division is exact, so every team's block is T of them)
   uint64_t stage_c = 0;
-  if (ksched == kDynamic || ksched == kChunked) stage_c = (uint64_t)chunk;
+  if (ksched == kDynamic || ksched == kChunked || ksched == kNonmono) stage_c = (uint64_t)chunk;
   if (ksched == kStatic && n % ((uint64_t)teams * (uint64_t)threads) == 0)
     stage_c = n / ((uint64_t)teams * (uint64_t)threads);
   if (stage_c) {

@@ -27,6 +27,7 @@ inline cudaError_t launch_sched(int sched, unsigned grid, unsigned block, size_t
     case kAuto: return launch_one<Body, Acc, kAuto>(grid, block, smem, st, a);
     case kDist: return launch_one<Body, Acc, kDist>(grid, block, smem, st, a);
     case kGuided: return launch_one<Body, Acc, kGuided>(grid, block, smem, st, a);
+    case kNonmono: return launch_one<Body, Acc, kNonmono>(grid, block, smem, st, a);
   }
   return cudaErrorNotSupported;
 }

@@ -11,7 +11,8 @@
 
 namespace rt {
 
-enum : int { kStatic = 0, kChunked = 1, kDynamic = 2, kAuto = 3, kDist = 4, kGuided = 5 };
+enum : int { kStatic = 0, kChunked = 1, kDynamic = 2, kAuto = 3, kDist = 4, kGuided = 5,
+             kNonmono = 6 };
 
 // Vectors each thread keeps in flight in the axpy body, and the largest team
 // the region kernels are compiled for (the register budget follows from it).
@@ -1026,6 +1027,34 @@ struct ClaimStatic {
   __device__ __forceinline__ unsigned long long next() { return (k++) * T + w32; }
 };
 
+// nonmonotonic dynamic: the team's groups of 32 chunks are split evenly
+// among its warps (next[v] / end[v], in shared memory); a warp claims from its
+// own range first, then from the other warps' ranges in turn.  A group is
+// claimed by one atomicAdd on a range's counter; the plain read before it only
+// skips ranges already used up (the add decides).  Returns the group's first
+// chunk, or nch when no group is left.
+struct ClaimNonmono {
+  unsigned long long* gnext;      // [W] next group of each warp's range
+  const unsigned long long* gend; // [W] end of each warp's range
+  uint32_t W, w;
+  unsigned long long nch;
+  __device__ __forceinline__ unsigned long long next() {
+    unsigned long long base = nch;
+    if (lane_id() == 0) {
+      for (uint32_t k = 0; k < W; ++k) {
+        const uint32_t v = w + k < W ? w + k : w + k - W;
+        if (*(volatile unsigned long long*)(gnext + v) >= gend[v]) continue;
+        const unsigned long long grp = atomicAdd(gnext + v, 1ull);
+        if (grp < gend[v]) {
+          base = grp * 32ull;
+          break;
+        }
+      }
+    }
+    return __shfl_sync(0xffffffffu, base, 0);
+  }
+};
+
 template <class Body, class Acc, class Claim>
 __device__ void run_staged(const Body& b, const RegionArgs& a, uint64_t bs, uint64_t bn,
                            uint64_t c, Claim claim, Acc& acc) {
@@ -1206,6 +1235,37 @@ __global__ void __launch_bounds__(OMPRT_MAX_THREADS) region_kernel(const RegionA
       last = run_guided(body, bs, bn, a.chunk ? a.chunk : 1, ctr, a.status, acc) && team_last;
       team_barrier();
       if (t == 0) *ctr = 0;  // leave the counter at zero for the next launch
+    } else if constexpr (SCHED == kNonmono) {
+      // nonmonotonic dynamic: per-warp ranges of chunk groups in shared memory
+      __shared__ unsigned long long nm_next[OMPRT_MAX_THREADS / 32], nm_end[OMPRT_MAX_THREADS / 32];
+      const uint64_t c = a.chunk;
+      const uint64_t nch = bn ? (bn - 1) / c + 1 : 0;
+      const uint32_t lane = lane_id(), w = warp_id(), W = T / 32;
+      if (lane == 0) {
+        uint64_t s0, cnt;
+        split_even((nch + 31) / 32, W, w, s0, cnt);
+        nm_next[w] = s0;
+        nm_end[w] = s0 + cnt;
+      }
+      team_barrier();  // every range is set before any warp steals
+      ClaimNonmono cl{nm_next, nm_end, W, w, nch};
+      bool staged = false;
+      if constexpr (Stageable<Body>::value) {
+        staged = a.stage_chunks != 0 && stage_ok(body, bs);
+        if (staged) run_staged(body, a, bs, bn, c, cl, acc);
+      }
+      constexpr bool kNarrow = !std::is_same<Body, BodyStencil1D>::value &&
+                               !std::is_same<Body, BodyStencil2D>::value;
+      while (!staged) {
+        const unsigned long long base = cl.next();
+        if (base >= nch) break;
+        const uint64_t j = base + lane;
+        if (j < nch) {
+          const uint64_t lo = j * c;
+          run_range<Body, Acc, kNarrow>(body, bs + lo, bs + (bn - lo > c ? lo + c : bn), acc);
+          if (j == nch - 1) last = team_last;
+        }
+      }
     } else {  // kDynamic: chunks of c claimed from this team's counter
       // pointwise bodies stream each lane's chunk with 128-bit accesses
       constexpr bool kNarrow = !std::is_same<Body, BodyStencil1D>::value &&

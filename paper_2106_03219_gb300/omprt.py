@@ -15,8 +15,8 @@ from . import build_lib
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOT_INIT, ERR_DEVICE = \
     range(8)
 DEV_STACK_NOMEM, DEV_STACK_ORDER, DEV_TIMEOUT, DEV_BAD_ARG = 0x1, 0x2, 0x4, 0x8
-SCHED_STATIC, SCHED_STATIC_CHUNKED, SCHED_DYNAMIC, SCHED_AUTO, SCHED_LEARNED, SCHED_GUIDED = \
-    range(6)
+SCHED_STATIC, SCHED_STATIC_CHUNKED, SCHED_DYNAMIC, SCHED_AUTO, SCHED_LEARNED, SCHED_GUIDED, \
+    SCHED_NONMONOTONIC = range(7)
 I32, U32, I64, U64, F32, BF16, F64 = range(7)
 OP_SUM, OP_MAX, OP_MIN = range(3)
 PREC_COMP_F64, PREC_COMP_F32, PREC_NAIVE_F32 = range(3)

@@ -168,3 +168,25 @@ def test_stencil2d_auto_fallbacks(rt):
                                O.exact_abs_sum_f32(want.reshape(-1)))
     assert ok, (err, bound)
     assert rt.sync_status() == 0
+
+
+@pytest.mark.parametrize("chunk,G,T", [(1, 7, 64), (7, 148, 256), (256, 64, 32), (64, 13, 1024)])
+def test_nonmonotonic_bodies_bit_exact(rt, chunk, G, T):
+    """axpy and both stencils under schedule(nonmonotonic: dynamic, c)."""
+    import torch
+    n = (1 << 20) + 13
+    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
+    xd, yd = dev(x), dev(y)
+    rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0), R.SCHED_NONMONOTONIC,
+                     chunk, G, T)
+    assert np.array_equal(bits32(host(yd)), bits32(O.axpy_f32(3.0, x, y)))
+    out = torch.full((n,), -7.0, device="cuda")
+    rt.launch_region(R.loop_desc(R.BODY_STENCIL1D3, n=n, x=xd, out=out), R.SCHED_NONMONOTONIC,
+                     chunk, G, T)
+    assert np.array_equal(bits32(host(out)), bits32(O.stencil1d3(x)))
+    a = inputs.grid_f32(129, 256, 6)
+    out2 = torch.full((129, 256), -7.0, device="cuda")
+    rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=129 * 256, x=dev(a), out=out2, nx=256,
+                                 ny=129), R.SCHED_NONMONOTONIC, chunk, G, T)
+    assert np.array_equal(bits32(host(out2)), bits32(O.stencil2d5(a)))
+    assert rt.sync_status() == 0

@@ -41,7 +41,8 @@ class Guarded:
 
 SCHEDS = [(R.SCHED_STATIC, 0), (R.SCHED_STATIC_CHUNKED, 1), (R.SCHED_STATIC_CHUNKED, 5),
           (R.SCHED_STATIC_CHUNKED, 64), (R.SCHED_DYNAMIC, 7), (R.SCHED_DYNAMIC, 256),
-          (R.SCHED_DYNAMIC, 8), (R.SCHED_AUTO, 0), (R.SCHED_GUIDED, 3)]
+          (R.SCHED_DYNAMIC, 8), (R.SCHED_AUTO, 0), (R.SCHED_GUIDED, 3),
+          (R.SCHED_NONMONOTONIC, 5), (R.SCHED_NONMONOTONIC, 64)]
 
 
 @pytest.mark.parametrize("sched,chunk", SCHEDS)

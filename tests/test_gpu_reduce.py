@@ -98,7 +98,8 @@ def test_dot_reduction(rt):
     x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
     r = _res()
     xd, yd = dev(x), dev(y)
-    for sched, chunk in ((R.SCHED_STATIC, 0), (R.SCHED_DYNAMIC, 256), (R.SCHED_AUTO, 0)):
+    for sched, chunk in ((R.SCHED_STATIC, 0), (R.SCHED_DYNAMIC, 256), (R.SCHED_AUTO, 0),
+                         (R.SCHED_NONMONOTONIC, 64), (R.SCHED_NONMONOTONIC, 256)):
         rt.launch_region(R.loop_desc(R.BODY_DOT, n=n, x=xd, y=yd), sched, chunk, 148,
                          256, red=R.ReduceDesc(R.OP_SUM, R.PREC_COMP_F64, r.data_ptr()))
         exact = O.exact_dot_f32(x, y)

@@ -75,6 +75,45 @@ def test_dynamic_invariants(rt, n, G, T, chunk):
 
 
 @pytest.mark.parametrize("n,G,T", CASES)
+@pytest.mark.parametrize("chunk", [1, 7, 64, 256])
+def test_nonmonotonic_invariants(rt, n, G, T, chunk):
+    """schedule(nonmonotonic: dynamic, c): the same invariants as dynamic
+    (every iteration once, whole chunks, chunks in the team, one last), with
+    no order required of a thread's chunks."""
+    owner, count, last = _map_record(rt, n, G, T, R.SCHED_NONMONOTONIC, chunk)
+    assert np.all(count == 1)
+    assert int((last == 1).sum()) == (1 if n else 0)
+    if n:
+        assert last[owner[n - 1]] == 1
+    for g in range(G):
+        bs, bn = O.static_nochunk(n, G, g)
+        blk = owner[bs:bs + bn]
+        assert np.all(blk // T == g)
+        idx = np.arange(bn)
+        same = (idx[1:] // chunk) == (idx[:-1] // chunk)
+        assert np.all(blk[1:][same] == blk[:-1][same])
+        # a claim is a group of 32 chunks, lane l of the claiming warp runs chunk
+        # 32 g + l: the owning lane of chunk j is j mod 32
+        if bn:
+            j = idx[::chunk] // chunk
+            assert np.all((blk[::chunk] % T) % 32 == j % 32)
+
+
+def test_nonmonotonic_warps_take_their_own_range_first(rt):
+    """One team of 8 warps and 8 * 32 groups of chunks, split evenly: a warp
+    claims from its own range first, so (unless it was scheduled so late that
+    another warp ran through a whole range first) the first group of range w
+    goes to warp w.  Required of at least half the warps."""
+    T, c = 256, 4
+    n = 8 * 32 * 32 * c
+    owner, count, last = _map_record(rt, n, 1, T, R.SCHED_NONMONOTONIC, c)
+    assert np.all(count == 1)
+    ng = n // (32 * c)
+    own = sum(int(owner[w * (ng // 8) * 32 * c] // 32 == w) for w in range(T // 32))
+    assert own >= 4, own
+
+
+@pytest.mark.parametrize("n,G,T", CASES)
 def test_auto_invariants(rt, n, G, T):
     owner, count, last = _map_record(rt, n, G, T, R.SCHED_AUTO, 0)
     assert np.all(count == 1)

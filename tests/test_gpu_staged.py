@@ -53,6 +53,11 @@ def test_axpy_f32_staged_bit_exact(staged, chunk, T, n):
     want = bits32(O.axpy_f32(3.0, x, y))
     for G in (1, 7, 64):
         assert np.array_equal(bits32(_axpy(rt, n, G, T, chunk, x, y)), want), G
+    for G in (1, 64):  # nonmonotonic dynamic takes the same staged path
+        xd, yd = dev(x), dev(y)
+        rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0),
+                         R.SCHED_NONMONOTONIC, chunk, G, T)
+        assert np.array_equal(bits32(host(yd)), want), ("nonmonotonic", G)
     rt.set_stage_bytes(0)  # plain form, same results
     assert np.array_equal(bits32(_axpy(rt, n, 7, T, chunk, x, y)), want)
     assert rt.sync_status() == 0
