@@ -804,6 +804,19 @@ __device__ __forceinline__ bool run_dist(const Body& b, uint64_t n, uint64_t d, 
       if (nd == nfull && nd && (nd - 1) % G == g && t == T - 1) last = true;
     }
   }
+  // dist_schedule(static, T) with schedule(static, 1), the usual GPU
+  // composite mapping: over the full distribute chunks thread t of team g
+  // runs iterations g*T + t + q*G*T, one stride-G*T sequence, which the
+  // scalar path runs in deep groups (one iteration per chunk at a time would
+  // keep a single load in flight)
+  if (j == g && c == 1 && d == T) {
+    const uint64_t nfull = n / d;
+    const uint64_t mine = g < nfull ? (nfull - 1 - g) / G + 1 : 0;
+    run_scalar<Body, Acc, StridedGroup<Body>::value>(b, (uint64_t)g * T + t, (uint64_t)G * T, mine,
+                                                     acc);
+    j = (nd > nfull && nfull % G == g) ? nfull : nd;
+    if (nd == nfull && nd && (nd - 1) % G == g && t == T - 1) last = true;
+  }
   for (; j < nd; j += G) {
     const uint64_t bs = j * d;
     const uint64_t bn = n - bs > d ? d : n - bs;
