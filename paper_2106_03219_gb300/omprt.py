@@ -36,6 +36,10 @@ class OmprtError(RuntimeError):
         super().__init__("%s: %s (status %d)" % (what, status_str(status), status))
 
 
+class LibraryMissing(RuntimeError):
+    """libomprt.so has not been built: there is no fallback."""
+
+
 class LoopDesc(C.Structure):
     _fields_ = [("lb", C.c_int64), ("ub", C.c_int64), ("incr", C.c_int64),
                 ("idx_type", C.c_int32), ("body", C.c_int32), ("data_type", C.c_int32),
@@ -105,8 +109,7 @@ def lib():
     if _lib is None:
         path = lib_path()
         if not os.path.exists(path):
-            raise OmprtError(ERR_NOT_INIT, "libomprt.so missing at %s; run "
-                             "__graft_entry__.build()" % path)
+            raise LibraryMissing("libomprt.so missing at %s; run __graft_entry__.build()" % path)
         L = C.CDLL(path)
         _declare(L)
         _lib = L

@@ -98,3 +98,13 @@ def test_host_trip_count_rejects(L):
         d = R.loop_desc(R.BODY_NONE, lb=lb, ub=ub, incr=incr, idx_type=t, data_type=R.F32)
         with pytest.raises(R.OmprtError):
             R.loop_trip_count(d)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: without the built library every call raises a clear error."""
+    monkeypatch.setattr(R, "_lib", None)
+    monkeypatch.setattr(R, "lib_path", lambda: "/nonexistent/libomprt.so")
+    with pytest.raises(R.LibraryMissing, match="libomprt.so missing"):
+        R.lib()
+    with pytest.raises(R.LibraryMissing):
+        R.Runtime(0)
