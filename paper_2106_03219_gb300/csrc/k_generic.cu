@@ -70,12 +70,38 @@ __global__ void __launch_bounds__(1024) generic_kernel(const GenericArgs A) {
     }
     team_barrier();  // hand-over: workers leave the wait state
     if (w_exit) break;
-    // the parallel region: parallel for over [lo, hi), static, no chunk
-    const uint64_t lo = w_lo, cnt_all = w_hi - w_lo;
-    uint64_t s, cnt;
-    split_even(cnt_all, T, t, s, cnt);
+    // the parallel region: parallel for over [lo, hi) under the default
+    // schedule, which OpenMP leaves to the implementation: static with a
+    // chunk of one 32-byte vector, round robin (a warp then covers 1 KB of
+    // contiguous memory per access; one contiguous piece per thread measured
+    // 0.77 of the copy rate for a dot over 2^14-element segments).  The
+    // iterations before the first 32-byte boundary and after the last run as
+    // scalars, round robin too.
+    const uint64_t lo = w_lo, hi = w_hi;
     AccCompF32 acc;
-    run_range(body, lo + s, lo + s + cnt, acc);
+    constexpr uint64_t V = Body::VEC;
+    uint64_t vlo = lo, vhi = lo;
+    if (body.vec_ok() && hi - lo >= V) {
+      vlo = (lo + V - 1) / V * V;
+      vhi = hi / V * V;
+      if (vhi < vlo) vhi = vlo;
+    }
+    run_strided(body, lo, vlo - lo, t, T, acc);  // head
+    {
+      typename Body::Frag f[2];
+      uint64_t v = vlo + (uint64_t)t * V;
+      for (; v + (uint64_t)T * V < vhi; v += 2ull * T * V) {  // two vectors in flight
+        body.load(v, f[0]);
+        body.load(v + (uint64_t)T * V, f[1]);
+        body.finish(v, f[0], acc);
+        body.finish(v + (uint64_t)T * V, f[1], acc);
+      }
+      if (v < vhi) {
+        body.load(v, f[0]);
+        body.finish(v, f[0], acc);
+      }
+    }
+    run_strided(body, vhi, hi - vhi, t, T, acc);  // tail
     const float2 v = team_reduce<AccCompF32>(acc.part(), scratch);
     if (t == 0) *w_var = __dadd_rn(*w_var, __dadd_rn((double)v.x, (double)v.y));
     team_barrier();  // join
