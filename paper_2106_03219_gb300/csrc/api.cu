@@ -429,6 +429,14 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
     if (e != cudaErrorNotSupported) return from_cuda(e);
     cudaGetLastError();
   }
+  if (d->body == OMPRT_BODY_STENCIL2D5 && ksched == kChunked && acc == kAccNone &&
+      d->data_type == OMPRT_F32 && c->stage_bytes != 0) {
+    e = launch_stencil2d_rows(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny,
+                              (uint64_t)chunk, (float)d->c0, (float)d->c1, (unsigned)teams,
+                              (unsigned)threads, c->max_smem_optin, c->status_dev, st);
+    if (e != cudaErrorNotSupported) return from_cuda(e);
+    cudaGetLastError();
+  }
   const bool f32path = d->data_type == OMPRT_F32 || d->data_type == OMPRT_BF16;
   if (d->body == OMPRT_BODY_MAP_RECORD || !f32path)
     e = launch_region_int(d->body, d->data_type, acc, ksched, (unsigned)teams, (unsigned)threads,

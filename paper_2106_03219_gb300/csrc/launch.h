@@ -40,6 +40,14 @@ cudaError_t launch_stencil2d_tiles(const void* in, float* out, uint64_t nx, uint
                                    float c1, unsigned teams, unsigned threads, uint32_t* status,
                                    cudaStream_t st);
 
+// static(c) 2-D stencil with the team's rows staged through a ring in shared
+// memory (k_stencil_rows.cu): c in [4, 8) and [32, 128], where it beats the
+// plain form; cudaErrorNotSupported (nothing launched) elsewhere.
+cudaError_t launch_stencil2d_rows(const void* in, float* out, uint64_t nx, uint64_t ny,
+                                  uint64_t chunk, float c0, float c1, unsigned teams,
+                                  unsigned threads, int max_smem, uint32_t* status,
+                                  cudaStream_t st);
+
 // Support kernels (k_support.cu).
 cudaError_t launch_static_table(uint64_t n, int64_t lb, int64_t incr, uint64_t chunk, unsigned G,
                                 unsigned T, int64_t* table, cudaStream_t st);

@@ -303,3 +303,52 @@ def test_staged_and_tiled_forms_in_a_cuda_graph(staged):
         assert np.array_equal(bits32(host(o1)), bits32(O.stencil1d3(a1)))
         assert np.array_equal(bits32(host(o2)), bits32(O.stencil2d5(g2)))
     assert rt.sync_status() == 0
+
+
+# -- static(c) 2-D stencil (c in [4, 8) and [32, 128]): the team walks its
+# block in passes of rows staged through a ring in shared memory; every thread
+# computes exactly its chunks, in 16-byte units where its piece allows.  The
+# other chunk sizes (and static without chunk) take the plain form.
+
+@pytest.mark.parametrize("ny,nx", [(1, 4), (2, 8), (9, 8), (33, 132), (67, 40), (100, 64),
+                                   (5, 16), (300, 1028)])
+@pytest.mark.parametrize("sched,chunk", [(R.SCHED_STATIC, 0), (R.SCHED_STATIC_CHUNKED, 1),
+                                         (R.SCHED_STATIC_CHUNKED, 4), (R.SCHED_STATIC_CHUNKED, 5),
+                                         (R.SCHED_STATIC_CHUNKED, 8),
+                                         (R.SCHED_STATIC_CHUNKED, 33),
+                                         (R.SCHED_STATIC_CHUNKED, 64),
+                                         (R.SCHED_STATIC_CHUNKED, 128),
+                                         (R.SCHED_STATIC_CHUNKED, 300)])
+def test_stencil2d_row_ring_bit_exact(staged, ny, nx, sched, chunk):
+    import torch
+    rt = staged
+    a = inputs.grid_f32(ny, nx, 6)
+    ad = dev(a)
+    want = bits32(O.stencil2d5(a))
+    for G, T in ((1, 32), (3, 64), (7, 96), (64, 256), (500, 32), (13, 1024), (5, 480)):
+        out = torch.full((ny, nx), -7.0, device="cuda")
+        rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=ny * nx, x=ad, out=out, nx=nx, ny=ny),
+                         sched, chunk, G, T)
+        assert np.array_equal(bits32(host(out)), want), (G, T)
+    assert rt.sync_status() == 0
+
+
+def test_stencil2d_row_ring_full_grid_and_off(staged):
+    """4096^2 at bench-like shapes, with the row ring and with staging off."""
+    import torch
+    rt = staged
+    a = inputs.grid_f32(4096, 4096, 0)
+    ad = dev(a)
+    want = bits32(O.stencil2d5(a))
+    for budget in (32768, 0):
+        rt.set_stage_bytes(budget)
+        for sched, chunk, G, T in ((R.SCHED_STATIC, 0, 8192, 128), (R.SCHED_STATIC_CHUNKED, 8,
+                                   1024, 1024), (R.SCHED_STATIC_CHUNKED, 64, 4096, 128),
+                                   (R.SCHED_STATIC_CHUNKED, 64, 2048, 128),
+                                   (R.SCHED_STATIC_CHUNKED, 4, 152, 1024),
+                                   (R.SCHED_STATIC_CHUNKED, 128, 456, 512)):
+            out = torch.empty_like(ad)
+            rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=4096 * 4096, x=ad, out=out, nx=4096,
+                                         ny=4096), sched, chunk, G, T)
+            assert np.array_equal(bits32(host(out)), want), (budget, sched, chunk, G, T)
+    assert rt.sync_status() == 0
