@@ -22,9 +22,12 @@ enum : int { kStatic = 0, kChunked = 1, kDynamic = 2, kAuto = 3, kDist = 4, kGui
 #ifndef OMPRT_MAX_THREADS
 #define OMPRT_MAX_THREADS 1024
 #endif
-// Vectors each thread keeps in flight in the value bodies of reductions.
+// Vectors each thread keeps in flight in the value bodies of reductions
+// (int32: at most 2; with 3 its extremum instances under auto spill).
+// Measured at n = 2^28 (L2 flushed), 3 against 2: fp32 max and min +6%,
+// bf16 sum +3%, fp32 and int64 sums unchanged.
 #ifndef OMPRT_LOAD_INFLIGHT
-#define OMPRT_LOAD_INFLIGHT 2
+#define OMPRT_LOAD_INFLIGHT 3
 #endif
 
 // Everything a region kernel needs, passed by value (one parameter block).
@@ -304,7 +307,7 @@ struct BodyLoadBF16 {
 struct BodyLoadI32 {
   static constexpr bool kVec = true;
   static constexpr int VEC = 8;
-  static constexpr int kInFlight = OMPRT_LOAD_INFLIGHT;
+  static constexpr int kInFlight = OMPRT_LOAD_INFLIGHT < 2 ? OMPRT_LOAD_INFLIGHT : 2;
   struct Frag { uint32_t x[8]; };
   const int32_t* x;
   __device__ explicit BodyLoadI32(const RegionArgs& r) : x((const int32_t*)r.x) {}
