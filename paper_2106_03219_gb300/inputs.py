@@ -117,3 +117,47 @@ def loop_set(count, seed, log2_lo=10, log2_hi=26):
     kind = g.integers(0, len(LOOP_KINDS), size=count).astype(np.int32)
     n = np.rint(np.exp2(g.uniform(log2_lo, log2_hi, size=count))).astype(np.int64)
     return kind, n
+
+
+# -- counter-based values for loops too large to draw on the host -------------
+# Value i of stream `seed` is a function of (i, seed) alone, so a device fill of
+# billions of elements and a host evaluation of a few sampled indices give the
+# same bytes.  The 32-bit mixer is the xor-shift-multiply integer hash with
+# multiplier 0x45d9f3b (T. Mueller); with a multiplier below 2^27 every
+# product of a 32-bit value stays below 2^59, so int64 arithmetic computes it
+# exactly in numpy and in torch alike.
+
+_M32 = 0xFFFFFFFF
+_MUL = 0x45D9F3B
+
+
+def _mix32(x):
+    x = x ^ (x >> 16)
+    x = (x * _MUL) & _M32
+    x = x ^ (x >> 16)
+    x = (x * _MUL) & _M32
+    return x ^ (x >> 16)
+
+
+def _hash_u32(i, seed):
+    """32-bit hash of index i (int64 array or tensor, 0 <= i < 2^62) and seed."""
+    hi = _mix32(((i >> 32) + 0x9E3779B9 * (seed + 1)) & _M32)
+    return _mix32((i & _M32) ^ hi)
+
+
+def counter_f32_01(idx, seed):
+    """fp32 in [0, 1) with 24 random bits (exact in fp32), at int64 indices idx."""
+    idx = np.asarray(idx, dtype=np.int64)
+    return ((_hash_u32(idx, seed) >> 8).astype(np.float64) * 2.0 ** -24).astype(np.float32)
+
+
+def counter_f32_01_fill(t, seed, start=0, block=1 << 26):
+    """Fill the 1-D fp32 tensor t (any device) with counter_f32_01(start + k,
+    seed), k = 0 .. t.numel() - 1, in blocks of `block` elements."""
+    import torch
+    n = t.numel()
+    for b in range(0, n, block):
+        e = min(b + block, n)
+        idx = torch.arange(start + b, start + e, dtype=torch.int64, device=t.device)
+        t[b:e] = (_hash_u32(idx, seed) >> 8).to(torch.float32) * (2.0 ** -24)
+    return t
