@@ -265,9 +265,11 @@ def test_stencil2d_staged_full_grid(staged):
 
 
 def test_staged_and_tiled_forms_in_a_cuda_graph(staged):
-    """Staged dynamic / static launches, a staged 1-D stencil and the
-    tensor-tiled 2-D stencil (its tensor map is a kernel parameter) captured
-    in one CUDA graph: every replay reproduces the eager results bit for bit."""
+    """Staged dynamic / static launches, a staged 1-D stencil, the
+    tensor-tiled 2-D stencil (its tensor map is a kernel parameter) and the
+    static(64) row ring on 4096-wide rows (96 KB of shared memory, opted in
+    at launch) captured in one CUDA graph: every replay reproduces the eager
+    results bit for bit."""
     import torch
     rt = staged
     n = (1 << 20) + 12
@@ -280,6 +282,9 @@ def test_staged_and_tiled_forms_in_a_cuda_graph(staged):
     g2 = inputs.grid_f32(1000, 1028, 6)
     g2d = dev(g2)
     o2 = torch.empty_like(g2d)
+    g3 = inputs.grid_f32(41, 4096, 7)
+    g3d = dev(g3)
+    o3 = torch.empty_like(g3d)
     s = torch.cuda.Stream()
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
@@ -291,17 +296,21 @@ def test_staged_and_tiled_forms_in_a_cuda_graph(staged):
                          R.SCHED_DYNAMIC, 64, 64, 32, stream=s)
         rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=1000 * 1028, x=g2d, out=o2, nx=1028,
                                      ny=1000), R.SCHED_AUTO, 0, 152, 256, stream=s)
+        rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=41 * 4096, x=g3d, out=o3, nx=4096,
+                                     ny=41), R.SCHED_STATIC_CHUNKED, 64, 9, 256, stream=s)
     want_y = O.axpy_f32(3.0, x, O.axpy_f32(3.0, x, y0))
     for _ in range(3):
         yd.copy_(dev(y0))
         o1.fill_(-7.0)
         o2.fill_(-7.0)
+        o3.fill_(-7.0)
         torch.cuda.synchronize()
         g.replay()
         torch.cuda.synchronize()
         assert np.array_equal(bits32(host(yd)), bits32(want_y))
         assert np.array_equal(bits32(host(o1)), bits32(O.stencil1d3(a1)))
         assert np.array_equal(bits32(host(o2)), bits32(O.stencil2d5(g2)))
+        assert np.array_equal(bits32(host(o3)), bits32(O.stencil2d5(g3)))
     assert rt.sync_status() == 0
 
 
