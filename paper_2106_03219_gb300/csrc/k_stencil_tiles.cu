@@ -147,20 +147,19 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// The driver's entry point is process-wide: looked up once, by the first
+// caller (a function-local static is initialised exactly once, thread-safely).
 static EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = nullptr;
-  static bool looked = false;
-  if (!looked) {
-    looked = true;
+  static const EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-    else
-      cudaGetLastError();
-  }
+      return (EncodeTiledFn)p;
+    cudaGetLastError();
+    return (EncodeTiledFn) nullptr;
+  }();
   return fn;
 }
 
@@ -202,24 +201,18 @@ cudaError_t launch_stencil2d_tiles(const void* in, float* out, uint64_t nx, uint
   const unsigned grid = teams < a.ntiles ? teams : a.ntiles;
   // warps per team: the largest of 1, 2, 4, 8 within the thread limit
   const unsigned warps = threads >= 256 ? 8 : threads >= 128 ? 4 : threads >= 64 ? 2 : 1;
+  auto* kern = warps == 8   ? stencil2d_tiles_kernel<8>
+               : warps == 4 ? stencil2d_tiles_kernel<4>
+               : warps == 2 ? stencil2d_tiles_kernel<2>
+                            : stencil2d_tiles_kernel<1>;
+  // the opt-in is a property of the kernel on the current device, so it is
+  // set at every launch (as for the region kernels), not cached per process
   if (kTileSmem > 48 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      const int b = (int)kTileSmem;
-      if (cudaFuncSetAttribute(stencil2d_tiles_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ||
-          cudaFuncSetAttribute(stencil2d_tiles_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ||
-          cudaFuncSetAttribute(stencil2d_tiles_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ||
-          cudaFuncSetAttribute(stencil2d_tiles_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))
-        return cudaGetLastError();
-      attr = true;
-    }
+    const cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    if (e != cudaSuccess) return e;
   }
-  switch (warps) {
-    case 8: stencil2d_tiles_kernel<8><<<grid, 256, kTileSmem, st>>>(map, a); break;
-    case 4: stencil2d_tiles_kernel<4><<<grid, 128, kTileSmem, st>>>(map, a); break;
-    case 2: stencil2d_tiles_kernel<2><<<grid, 64, kTileSmem, st>>>(map, a); break;
-    default: stencil2d_tiles_kernel<1><<<grid, 32, kTileSmem, st>>>(map, a); break;
-  }
+  kern<<<grid, 32 * warps, kTileSmem, st>>>(map, a);
   return cudaGetLastError();
 }
 
