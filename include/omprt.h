@@ -197,9 +197,15 @@ omprt_status omprt_alloc_shared(omprt_ctx *ctx, size_t bytes_per_team);
  * reaches one element / one row beyond the pass, when the chunk is at most
  * 512 bytes and the two halos at most a quarter of the pass.  A claim of 32
  * chunks runs in equal passes.  Other launches, and teams whose block does
- * not start on a 16-byte boundary, run the plain form.  bytes is rounded down to
- * 16; 0 turns staging off; more than the device's per-block shared memory is
- * OMPRT_ERR_INVALID.  Default after init: 32 KiB. */
+ * not start on a 16-byte boundary, run the plain form.  The 2-D stencil under
+ * static(c) with c in [4, 8) or [32, 128] (fp32, no reduction, nx a multiple of
+ * 4, n < 2^32, 16-byte-aligned pointers) instead walks each team's block in
+ * passes of two rows through a six-row ring in shared memory (six rows of nx
+ * floats, which must fit the device's per-block shared memory, whatever
+ * `bytes`); every thread still runs exactly its own chunks.  bytes is rounded
+ * down to 16; 0 turns every staged form, the row ring included, off; more than
+ * the device's per-block shared memory is OMPRT_ERR_INVALID.  Default after
+ * init: 32 KiB. */
 omprt_status omprt_set_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_team);
 
 /*
