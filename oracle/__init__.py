@@ -7,6 +7,7 @@ marshals numpy arrays and forwards to the C routine that states the reading
 of the paper it follows.
 """
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -19,9 +20,12 @@ TYPE_NAMES = {"i32": I32, "u32": U32, "i64": I64, "u64": U64}
 
 
 def lib():
+    """The built oracle.  OMPRT_ORACLE_LIB names another build of the same
+    source to load instead: the mutation tests load copies with one planted
+    mistake each and check that the pins fail on them."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
+        _lib = C.CDLL(os.environ.get("OMPRT_ORACLE_LIB") or _build.build())
         _declare(_lib)
     return _lib
 

@@ -120,3 +120,28 @@ def test_max_min():
     c = inputs.int32_uniform(5000, 4)
     assert O.max_min(c, "max") == max(c.tolist())
     assert O.max_min(c, "min") == min(c.tolist())
+
+
+def test_max_min_one_sided_single_and_empty():
+    """Arrays entirely below zero (max) or above zero (min), single elements at
+    the type's extremes, and the empty array, whose result is the identity of
+    the operation (OpenMP's initializer for max / min: the least / greatest
+    value of the type)."""
+    f = np.abs(inputs.f32_uniform_pm1(3000, 5)) + np.float32(0.25)
+    for a in (f, -f):
+        assert O.max_min(a, "max") == float(max(a.tolist()))
+        assert O.max_min(a, "min") == float(min(a.tolist()))
+    for dt, lo, hi in ((np.int32, -(1 << 31), (1 << 31) - 1), (np.int64, -(1 << 63), (1 << 63) - 1)):
+        pos = np.abs(inputs.int32_uniform(3000, 6)).astype(dt) + 1
+        for a in (pos, -pos):
+            assert O.max_min(a, "max") == max(a.tolist())
+            assert O.max_min(a, "min") == min(a.tolist())
+        for v in (lo, hi, -1, 1):
+            one = np.array([v], dt)
+            assert O.max_min(one, "max") == v and O.max_min(one, "min") == v
+        empty = np.zeros(0, dt)
+        assert O.max_min(empty, "max") == lo and O.max_min(empty, "min") == hi
+    one = np.array([-3.5], np.float32)
+    assert O.max_min(one, "max") == -3.5 and O.max_min(one, "min") == -3.5
+    empty = np.zeros(0, np.float32)
+    assert O.max_min(empty, "max") == float("-inf") and O.max_min(empty, "min") == float("inf")
