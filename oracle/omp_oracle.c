@@ -375,9 +375,12 @@ int64_t orc_min_i64(uint64_t n, const int64_t *a)
     return m;
 }
 
+/* int32 data reduce into the int64 result the entry point writes; an empty
+ * loop gives the identity of that result type (OpenMP's max / min
+ * initializer: the least / greatest value of the reduction item's type). */
 int64_t orc_max_i32(uint64_t n, const int32_t *a)
 {
-    int64_t m = INT32_MIN;
+    int64_t m = INT64_MIN;
     for (uint64_t i = 0; i < n; i++)
         if (a[i] > m) m = a[i];
     return m;
@@ -385,7 +388,7 @@ int64_t orc_max_i32(uint64_t n, const int32_t *a)
 
 int64_t orc_min_i32(uint64_t n, const int32_t *a)
 {
-    int64_t m = INT32_MAX;
+    int64_t m = INT64_MAX;
     for (uint64_t i = 0; i < n; i++)
         if (a[i] < m) m = a[i];
     return m;

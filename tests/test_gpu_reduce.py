@@ -56,6 +56,28 @@ def test_max_min_exact(rt, n):
             assert host(r)[0] == O.max_min(a, name)
 
 
+@pytest.mark.parametrize("G,T", [(1, 32), (37, 256), (608, 512)])
+def test_max_min_one_sided_and_empty(rt, G, T):
+    """Arrays entirely below zero under max and above zero under min (a wrong
+    starting value shows there), and n = 0, whose result is the identity in
+    the result's type: -inf / +inf (fp32 data, double result),
+    INT64_MIN / INT64_MAX (int32 and int64 data, int64 result).  The result
+    buffer starts at a sentinel, so the launch must write it."""
+    import torch
+    f = np.abs(inputs.f32_uniform_pm1(5000, 5)) + np.float32(0.25)
+    p32 = np.abs(inputs.int32_uniform(5000, 6)) + 1
+    cases = [f, -f, p32, -p32, p32.astype(np.int64) << 20, -(p32.astype(np.int64) << 20),
+             np.zeros(0, np.float32), np.zeros(0, np.int32), np.zeros(0, np.int64)]
+    for a in cases:
+        for op, name in ((R.OP_MAX, "max"), (R.OP_MIN, "min")):
+            fl = a.dtype == np.float32
+            r = torch.full((1,), 12345, dtype=torch.float64 if fl else torch.int64, device="cuda")
+            rt.reduce(op, dev(a), r, 0, G, T)
+            got = host(r)[0]
+            assert (float(got) if fl else int(got)) == O.max_min(a, name), (a.dtype, a.size, name)
+    assert rt.sync_status() == 0
+
+
 def test_bf16_sum(rt):
     bits = inputs.bf16_uniform_pm1((1 << 20) + 11, 5)
     r = _res()

@@ -62,7 +62,9 @@ MUTANTS = [
     # C7 reductions
     ("sum_i32_zero_extends", "s += (uint64_t)(int64_t)a[i];", "s += (uint64_t)(uint32_t)a[i];"),
     ("max_f32_start", "double m = -INFINITY;", "double m = 0.0;"),
-    ("min_i32_start", "int64_t m = INT32_MAX;", "int64_t m = 0;"),
+    ("min_i32_start",
+     "int64_t orc_min_i32(uint64_t n, const int32_t *a)\n{\n    int64_t m = INT64_MAX;",
+     "int64_t orc_min_i32(uint64_t n, const int32_t *a)\n{\n    int64_t m = 0;"),
     ("exact_round_ties_away",
      "if (rem > 0x400 || (rem == 0x400 && (sticky || (mant & 1)))) mant++;",
      "if (rem >= 0x400) mant++;"),

@@ -125,8 +125,9 @@ def test_max_min():
 def test_max_min_one_sided_single_and_empty():
     """Arrays entirely below zero (max) or above zero (min), single elements at
     the type's extremes, and the empty array, whose result is the identity of
-    the operation (OpenMP's initializer for max / min: the least / greatest
-    value of the type)."""
+    the operation in the result's type (OpenMP's initializer for max / min:
+    the least / greatest value of the reduction item's type; integer data
+    reduce into an int64 result, fp32 data into a double)."""
     f = np.abs(inputs.f32_uniform_pm1(3000, 5)) + np.float32(0.25)
     for a in (f, -f):
         assert O.max_min(a, "max") == float(max(a.tolist()))
@@ -140,7 +141,7 @@ def test_max_min_one_sided_single_and_empty():
             one = np.array([v], dt)
             assert O.max_min(one, "max") == v and O.max_min(one, "min") == v
         empty = np.zeros(0, dt)
-        assert O.max_min(empty, "max") == lo and O.max_min(empty, "min") == hi
+        assert O.max_min(empty, "max") == -(1 << 63) and O.max_min(empty, "min") == (1 << 63) - 1
     one = np.array([-3.5], np.float32)
     assert O.max_min(one, "max") == -3.5 and O.max_min(one, "min") == -3.5
     empty = np.zeros(0, np.float32)
