@@ -78,6 +78,9 @@ def test_host_trip_count_matches_oracle(L, t):
                 cases.append((lb, ub, incr))
     for incr in (1, 3, 1 << 20):
         cases += [(tmax - 10, tmax, incr), (tmin + 10, tmin, -incr), (tmin, tmax, incr * 97)]
+    # increments at and past what a 32-bit index type holds
+    for incr in ((1 << 31) - 1, 1 << 31, 1 << 40):
+        cases += [(tmin, tmax, incr), (tmax, tmin, -incr)]
     for lb, ub, incr in cases:
         d = R.loop_desc(R.BODY_NONE, lb=lb, ub=ub, incr=incr, idx_type=R.TYPE_CODES[t],
                         data_type=R.F32)

@@ -29,6 +29,11 @@ MUTANTS = [
     ("trip_count_signedness",
      "empty = incr > 0 ? (ub < lb) : (ub > lb);",
      "empty = incr > 0 ? ((uint64_t)ub < (uint64_t)lb) : ((uint64_t)ub > (uint64_t)lb);"),
+    ("widen_u32_sign_extends", "if (type == ORC_U32) return (int64_t)(uint32_t)v;",
+     "if (type == ORC_U32) return (int64_t)(int32_t)v;"),
+    ("incr_limit_unchecked",
+     "if ((type == ORC_I32 || type == ORC_U32) && (incr > INT32_MAX || incr < -INT32_MAX))",
+     "if (0 && (type == ORC_I32 || type == ORC_U32) && (incr > INT32_MAX || incr < -INT32_MAX))"),
     # C1 static without chunk
     ("static_start_index", "*start = k * q + (k < r ? k : r);", "*start = k * q + (k < r ? k : 0);"),
     ("static_count_drops_remainder", "*count = q + (k < r ? 1 : 0);", "*count = q;"),
@@ -37,7 +42,9 @@ MUTANTS = [
     ("chunk_last_owner", "*last = (nch > 0 && k == (nch - 1) % P);", "*last = (nch > 0 && k == nch % P);"),
     ("nochunk_stride", "*stride = orc_mul(bn, incr);", "*stride = orc_mul(bn - 1, incr);"),
     ("empty_piece_UB", "orc_add(*LB, -incr);", "orc_add(*LB, incr);"),
-    # C3 owner maps
+    # C3 composite table and owner maps
+    ("composite_team_columns_swapped", "row[0] = tLB; row[1] = tUB; row[2] = tst; row[3] = tlast;",
+     "row[0] = tUB; row[1] = tLB; row[2] = tst; row[3] = tlast;"),
     ("owner_map_chunk_end",
      "uint64_t a = j * chunk;\n                    uint64_t e = (bn - a > chunk) ? a + chunk : bn;",
      "uint64_t a = j * chunk;\n                    uint64_t e = (bn - a > chunk) ? a + chunk - 1 : bn;"),
@@ -75,6 +82,8 @@ MUTANTS = [
      "a->d[k] -= (int64_t)((uint64_t)c << 31);"),
     ("exact_add_sign_of_top_digit", "if (v < 0) { d0 = -d0; d1 = -d1; d2 = -d2; }",
      "if (v < 0) { d0 = -d0; d1 = -d1; }"),
+    ("exact_round_drops_sign", "return neg ? -r : r;", "return r;"),
+    ("abs_sum_without_abs", "kl_add(&acc, fabs((double)a[i]));", "kl_add(&acc, (double)a[i]);"),
     ("bf16_decode_shift", "uint32_t bits = (uint32_t)a[i] << 16;", "uint32_t bits = (uint32_t)a[i] << 15;"),
     ("dot_transposed_operand", "kl_add(&acc, (double)x[i] * (double)y[i]);",
      "kl_add(&acc, (double)x[i] * (double)x[i]);"),
@@ -85,14 +94,22 @@ MUTANTS = [
      "uint64_t r = (b + 15) / 16 * 16;"),
     ("stack_free_order_unchecked", "if (region == 0 && off + r == top_s) top_s = off;",
      "if (region == 0) top_s = off;"),
+    ("stack_nomem_bit_dropped", "region = 2; status |= ORC_STACK_NOMEM;", "region = 2;"),
+    ("stack_free_of_failed_alloc_flagged", "else if (region == 2) bits = 0;",
+     "else if (region == 2) bits = ORC_STACK_ORDER;"),
     ("stack_pool_capacity", "} else if (r <= Q - top_q && top_q <= Q) {",
      "} else if (r <= Q && top_q <= Q) {"),
     # C12 MLP and Adam
     ("mlp_relu_dropped", "out[o] = (relu && s < 0.0) ? 0.0 : s;", "out[o] = s;"),
+    ("mlp_output_layer_relu",
+     "mlp_layer(p + OFF_W3, p + OFF_B3, h2, M_H, M_OUT, 0, Y + r * M_OUT);",
+     "mlp_layer(p + OFF_W3, p + OFF_B3, h2, M_H, M_OUT, 1, Y + r * M_OUT);"),
     ("mlp_grad_w2_transposed", "grad[OFF_W2 + o * M_H + i] += dh2[o] * h1[i];",
      "grad[OFF_W2 + i * M_H + o] += dh2[o] * h1[i];"),
     ("mlp_backprop_relu_gate", "dh1[i] = h1[i] > 0.0 ? s : 0.0;", "dh1[i] = s;"),
     ("mlp_loss_grad_factor", "dy[o] = 2.0 * d * scale;", "dy[o] = d * scale;"),
+    ("adam_second_moment_not_squared", "v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];",
+     "v[i] = b2 * v[i] + (1.0 - b2) * g[i];"),
     ("adam_bias_correction", "double mh = m[i] / c1, vh = v[i] / c2;",
      "double mh = m[i], vh = v[i] / c2;"),
 ]

@@ -97,6 +97,22 @@ def test_trip_count_rejects():
         O.trip_count(0, (1 << 64) - 1, 1, "u64")    # 2^64 iterations
 
 
+@pytest.mark.parametrize("t", ["i32", "u32"])
+def test_trip_count_increment_must_fit_the_index_type(t):
+    """A 32-bit loop variable cannot step by an increment its type cannot hold
+    (its negation too, for a decreasing loop): |incr| <= 2^31 - 1 is a loop,
+    2^31 is rejected either way; the 64-bit types take any non-zero increment."""
+    lo, hi = (-(1 << 31), (1 << 31) - 1) if t == "i32" else (0, (1 << 32) - 1)
+    for incr in (1 << 31, -(1 << 31), 1 << 40, -(1 << 40)):
+        with pytest.raises(O.OracleError):
+            O.trip_count(lo if incr > 0 else hi, hi if incr > 0 else lo, incr, t)
+    big = (1 << 31) - 1
+    assert O.trip_count(lo, hi, big, t) == brute_trip(lo, hi, big)
+    assert O.trip_count(hi, lo, -big, t) == brute_trip(hi, lo, -big)
+    for t64 in ("i64", "u64"):
+        assert O.trip_count(0, 1 << 40, 1 << 31, t64) == brute_trip(0, 1 << 40, 1 << 31)
+
+
 # -- C1 / C2 -----------------------------------------------------------------------
 
 def test_static_nochunk_vs_dealing():
