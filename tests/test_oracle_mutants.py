@@ -6,7 +6,8 @@ wrong index or a transposed operand.  The copy is compiled to its own library
 and the oracle pin tests (tests/test_oracle_*.py) run against it through the
 OMPRT_ORACLE_LIB hook; at least one pin must fail.  A mutant that survives
 names a reading of the paper that no pin holds the oracle to.  No mutant can
-loop forever or read outside its arrays.
+loop forever or read outside its arrays, and none is equivalent to the
+original (a replacement that cannot change any result is left out).
 """
 import concurrent.futures as cf
 import os
@@ -40,6 +41,9 @@ MUTANTS = [
     # C2 static chunk
     ("chunk_stride_drops_P", "*stride = orc_mul(P * c, incr);", "*stride = orc_mul(c, incr);"),
     ("chunk_last_owner", "*last = (nch > 0 && k == (nch - 1) % P);", "*last = (nch > 0 && k == nch % P);"),
+    ("chunk_count_floor", "uint64_t nch = bn == 0 ? 0 : (bn - 1) / c + 1;",
+     "uint64_t nch = bn == 0 ? 0 : bn / c;"),
+    ("last_chunk_full_length", "cnt = (bn - s > c) ? c : bn - s;", "cnt = c;"),
     ("nochunk_stride", "*stride = orc_mul(bn, incr);", "*stride = orc_mul(bn - 1, incr);"),
     ("empty_piece_UB", "orc_add(*LB, -incr);", "orc_add(*LB, incr);"),
     # C3 composite table and owner maps
@@ -48,6 +52,9 @@ MUTANTS = [
     ("owner_map_chunk_end",
      "uint64_t a = j * chunk;\n                    uint64_t e = (bn - a > chunk) ? a + chunk : bn;",
      "uint64_t a = j * chunk;\n                    uint64_t e = (bn - a > chunk) ? a + chunk - 1 : bn;"),
+    ("dist_chunk_end",
+     "uint64_t a = k * chunk;\n                    uint64_t e = (bn - a > chunk) ? a + chunk : bn;",
+     "uint64_t a = k * chunk;\n                    uint64_t e = (bn - a > chunk) ? a + chunk - 1 : bn;"),
     ("dist_team_of_chunk", "uint64_t g = j % G;", "uint64_t g = (j + 1) % G;"),
     # guided
     ("guided_divisor", "uint64_t want = (r + 2 * T - 1) / (2 * T);",
@@ -80,6 +87,8 @@ MUTANTS = [
      "if (rem > 0x400 || (rem == 0x400 && (mant & 1))) mant++;"),
     ("exact_carry_shift", "a->d[k] -= (int64_t)((uint64_t)c << 32);",
      "a->d[k] -= (int64_t)((uint64_t)c << 31);"),
+    ("exact_add_high_digit_shift", "uint64_t hi = sh ? (m >> (64 - sh)) : 0;",
+     "uint64_t hi = sh ? (m >> (63 - sh)) : 0;"),
     ("exact_add_sign_of_top_digit", "if (v < 0) { d0 = -d0; d1 = -d1; d2 = -d2; }",
      "if (v < 0) { d0 = -d0; d1 = -d1; }"),
     ("exact_round_drops_sign", "return neg ? -r : r;", "return r;"),
