@@ -8,7 +8,6 @@ lognormal, clipped to [100, 10^6]; each region is an fp32 axpy, an fp32 dot
 product with a sum reduction, or a 1-D 3-point stencil, on disjoint slices of
 one allocation.
 """
-import numpy as np
 
 from . import inputs
 from . import omprt as R

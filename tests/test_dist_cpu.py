@@ -3,7 +3,6 @@ maximum time over ranks (what bench.py divides the whole-job bytes by)."""
 import os
 import socket
 
-import pytest
 
 
 def _free_port():

@@ -96,7 +96,6 @@ def test_map_record_and_reductions_stay_in_bounds(rt, n):
 
 
 def test_dist_batch_generic_stay_in_bounds(rt):
-    import torch
     n, off = 30011, 3
     x = dev(inputs.f32_uniform01(n, 0))
     y = Guarded(n, np.float32, off, inputs.f32_uniform01(n, 1))

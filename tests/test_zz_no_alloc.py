@@ -11,7 +11,6 @@ omprt_reduce on the same data, within the tolerance the reduction tests use
 reference call, so it runs the same alone in a fresh process or after the
 other tests.
 """
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
