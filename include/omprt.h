@@ -172,7 +172,10 @@ typedef struct omprt_ctx omprt_ctx;
  * failure with *ctx untouched. */
 omprt_status omprt_init(int device, omprt_ctx **ctx);
 
-/* Free the context's scratch.  The caller must have synchronised its streams. */
+/* Free what omprt_init allocated: the context's scratch on the device (the
+ * runtime's per-device state, Sec. 3.1) and the context itself.  The caller
+ * must have synchronised its streams; ctx is invalid afterwards.  NULL is
+ * OMPRT_ERR_NOT_INIT. */
 omprt_status omprt_finalize(omprt_ctx *ctx);
 
 /* Reserve the per-team shared-memory stack capacity S for later launches
@@ -264,8 +267,14 @@ omprt_status omprt_launch_generic(omprt_ctx *ctx, const int64_t *seg_dev, int64_
                                   int32_t num_teams, int32_t thread_limit, void *stream);
 
 /* reduction(op) over n elements of dtype (F32, BF16, I32, I64) at data_dev:
- * omprt_launch_region with BODY_NONE and schedule AUTO.  result_dev: 8 bytes
- * (double for F32/BF16, int64 for integers).  precision: omprt_precision. */
+ * omprt_launch_region with BODY_NONE and schedule AUTO, the reduction clause of
+ * the worksharing loop the runtime divides (Sec. 1, Sec. 2); team partials
+ * cross teams through the flush of Listing 2 and the atomic inc of Listing 3
+ * (Sec. 3.1).  data_dev and result_dev are device pointers the caller owns;
+ * result_dev: 8 bytes (double for F32/BF16, int64 for integers), written by
+ * the launch (n = 0 writes the operation's identity in that type).
+ * precision: omprt_precision.  Bad arguments return OMPRT_ERR_INVALID and
+ * launch nothing. */
 omprt_status omprt_reduce(omprt_ctx *ctx, int32_t op, int32_t dtype, int32_t precision,
                           const void *data_dev, int64_t n, void *result_dev,
                           int32_t num_teams, int32_t thread_limit, void *stream);
@@ -280,21 +289,26 @@ omprt_status omprt_static_init_table(omprt_ctx *ctx, const omprt_loop_desc *desc
                                      int32_t num_teams, int32_t thread_limit, int64_t *table_dev,
                                      void *stream);
 
-/* Host-only: the trip count n of desc's loop (rule above: bounds compared in
- * the loop variable's signedness, distance in unsigned 64-bit arithmetic).
+/* Host-only: the trip count n of desc's loop, the iterations the runtime's
+ * worksharing routines divide (Sec. 2).  Rule above: bounds compared in
+ * the loop variable's signedness, distance in unsigned 64-bit arithmetic;
+ * a 32-bit index type takes |incr| <= 2^31 - 1.
  * Returns OMPRT_ERR_INVALID for a bad type, bound or incr == 0 and
  * OMPRT_ERR_UNSUPPORTED for 2^63 or more iterations.  Needs no device. */
 omprt_status omprt_loop_trip_count(const omprt_loop_desc *desc, uint64_t *n_host);
 
 /* Synchronise `stream`, then read and clear the sticky device status word.
  * *bits_host (may be NULL) receives the OMPRT_DEV_* bits.  Returns
- * OMPRT_ERR_DEVICE if any bit was set, OMPRT_ERR_CUDA if the sync failed. */
+ * OMPRT_ERR_DEVICE if any bit was set, OMPRT_ERR_CUDA if the sync failed.
+ * Not a routine of the paper's runtime: this library's way to report what
+ * its device code checks (bounded waits, stack overflow, bad arguments). */
 omprt_status omprt_sync_status(omprt_ctx *ctx, void *stream, uint32_t *bits_host);
 
 /* Static description of a status code. */
 const char *omprt_status_str(omprt_status s);
 
-/* Number of SMs of the context's device (0 for a NULL context). */
+/* Number of SMs of the context's device (0 for a NULL context).  A query of
+ * this library, not a routine of the paper's runtime. */
 int32_t omprt_sm_count(const omprt_ctx *ctx);
 
 /* ------------------------------------------------------------------ */
@@ -354,7 +368,9 @@ omprt_status omprt_batch_create(omprt_ctx *ctx, const omprt_loop_desc *descs_hos
 omprt_status omprt_launch_batch(omprt_batch *batch, int32_t num_ctas, int32_t threads,
                                 void *stream);
 omprt_status omprt_batch_destroy(omprt_batch *batch);
-/* Number of work items (chunks) in the batch; 0 for NULL. */
+/* Number of work items (chunks) in the batch; 0 for NULL.  The batch is the
+ * many-short-regions case of Sec. 4.3 (miniQMC's target regions launched tens
+ * of thousands of times), run as one launch. */
 int64_t omprt_batch_items(const omprt_batch *batch);
 
 /* ------------------------------------------------------------------ */
@@ -381,7 +397,8 @@ omprt_status omprt_test_barrier(omprt_ctx *ctx, int32_t num_teams, int32_t threa
                                 int32_t sub_threads, int32_t rounds, uint32_t *errors_dev,
                                 void *stream);
 
-/* Bounded device wait (the runtime has no unbounded wait): thread 0 of each
+/* Bounded device wait, the synchronization the target-specific part provides
+ * (Sec. 3.2), with a limit (the runtime has no unbounded wait): thread 0 of each
  * of num_teams teams waits until *flag_dev == expect or timeout_us
  * microseconds (1 .. 2,000,000) pass on the GPU timer; out_dev[g] = 1 if the
  * value was seen, 0 if the wait gave up, in which case OMPRT_DEV_TIMEOUT is
@@ -404,7 +421,12 @@ omprt_status omprt_test_stack(omprt_ctx *ctx, int32_t num_teams, int64_t stack_b
 /* ------------------------------------------------------------------ */
 /* Learned schedule: MLP cost model 16 -> 64 -> 64 -> 12 (fp32)        */
 /* ------------------------------------------------------------------ */
-/* Parameter vector layout (float32, 6028 values): W1[64][16], b1[64],
+/* Not a routine of the paper's runtime: a learned choice of schedule, chunk,
+ * teams and threads for the loops the runtime divides (Sec. 2), added by this
+ * library.  Every entry point below takes device pointers the caller owns
+ * (params, inputs, gradients, Adam moments) unless it says host; bad sizes or
+ * NULL pointers return OMPRT_ERR_INVALID and launch nothing.
+ * Parameter vector layout (float32, 6028 values): W1[64][16], b1[64],
  * W2[64][64], b2[64], W3[12][64], b3[12], row-major W[out][in].
  * h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3. */
 #define OMPRT_MLP_IN 16
