@@ -314,7 +314,8 @@ int32_t omprt_sm_count(const omprt_ctx *ctx);
 /* ------------------------------------------------------------------ */
 /* Reduction without any allocation                                    */
 /* ------------------------------------------------------------------ */
-/* The paper has no counterpart to this call; it exists for callers of this
+/* The paper has no counterpart to this call (it is a reduction clause over
+ * the loop the runtime divides, Sec. 2, like omprt_reduce); it exists for callers of this
  * library that cannot allocate device memory: code running while a CUDA
  * graph is being captured, inside a stream callback or an allocator hook,
  * under a lock that cudaMalloc could need, or in a process whose device
@@ -363,8 +364,12 @@ typedef struct omprt_batch omprt_batch;
 omprt_status omprt_batch_create(omprt_ctx *ctx, const omprt_loop_desc *descs_host,
                                 const omprt_reduce_desc *reds_host, int32_t nregions,
                                 int64_t chunk_elems, omprt_batch **batch);
-/* num_ctas 0 = SMs x resident CTAs per SM; threads: multiple of 32 in
- * [64, 1024], 0 = 256. */
+/* Run the batch: every region in one persistent launch (the many short
+ * target regions of Sec. 4.3 as one launch; the work queue is claimed with the
+ * atomic add of Sec. 3.1).  num_ctas 0 = SMs x resident CTAs per SM; threads:
+ * multiple of 32 in [64, 1024], 0 = 256.  omprt_batch_destroy frees the
+ * batch's device table and queue (the caller has synchronised its streams);
+ * NULL is OMPRT_ERR_INVALID. */
 omprt_status omprt_launch_batch(omprt_batch *batch, int32_t num_ctas, int32_t threads,
                                 void *stream);
 omprt_status omprt_batch_destroy(omprt_batch *batch);
@@ -434,29 +439,34 @@ omprt_status omprt_test_stack(omprt_ctx *ctx, int32_t num_teams, int64_t stack_b
 #define OMPRT_MLP_OUT 12
 #define OMPRT_MLP_NPARAM 6028
 
-/* y_dev[B][12] = model(x_dev[B][16]). */
+/* y_dev[B][12] = model(x_dev[B][16]) (learned schedule: this library's own,
+ * not a routine of the paper's runtime). */
 omprt_status omprt_mlp_forward(omprt_ctx *ctx, const float *params_dev, const float *x_dev,
                                int32_t batch, float *y_dev, void *stream);
-/* Mean-squared-error loss over the batch and the 12 outputs and its gradient:
+/* (Learned schedule: this library's own, not a routine of the paper's
+ * runtime.)  Mean-squared-error loss over the batch and the 12 outputs and its gradient:
  * grad_dev[6028] = d loss / d params (overwritten), loss_dev[1] (may be NULL).
  * batch in [1, 16384]; the per-sample activations go to context scratch, so
  * calls on one context must not overlap on the device. */
 omprt_status omprt_mlp_loss_grad(omprt_ctx *ctx, const float *params_dev, const float *x_dev,
                                  const float *target_dev, int32_t batch, float *grad_dev,
                                  float *loss_dev, void *stream);
-/* One bias-corrected Adam step (Kingma & Ba 2015) at step number t >= 1 on
+/* (Learned schedule: this library's own, not a routine of the paper's
+ * runtime.)  One bias-corrected Adam step (Kingma & Ba 2015) at step number t >= 1 on
  * params_dev, with moment buffers m_dev, v_dev (zero before step 1). */
 omprt_status omprt_mlp_adam(omprt_ctx *ctx, float *params_dev, const float *grad_dev,
                             float *m_dev, float *v_dev, int32_t n, int32_t t, float lr,
                             float beta1, float beta2, float eps, void *stream);
 
-/* Learned-schedule configuration table: index k in [0, 12) of the model's
+/* (Learned schedule: this library's own, not a routine of the paper's
+ * runtime.)  Configuration table: index k in [0, 12) of the model's
  * output is configuration k: sched_host[k], chunk_host[k], teams_per_sm_host[k]
  * (num_teams = teams_per_sm * SMs) and threads_host[k]; any pointer may be NULL. */
 omprt_status omprt_learned_configs(int32_t *sched_host, int64_t *chunk_host,
                                    int32_t *teams_per_sm_host, int32_t *threads_host);
 
-/* Install (params_host != NULL) or remove (NULL) the cost model used by
+/* (Learned schedule: this library's own, not a routine of the paper's
+ * runtime.)  Install (params_host != NULL) or remove (NULL) the cost model used by
  * OMPRT_SCHED_LEARNED, with the feature standardisation (mean_host[16],
  * std_host[16]).  The model is copied; inference runs on the host at launch
  * time, takes the argmin of the 12 predicted log-times, and falls back to the
@@ -464,8 +474,14 @@ omprt_status omprt_learned_configs(int32_t *sched_host, int64_t *chunk_host,
 omprt_status omprt_set_cost_model(omprt_ctx *ctx, const float *params_host,
                                   const float *mean_host, const float *std_host);
 
-/* Features (16 floats) the cost model sees for a loop, and the configuration
- * index the installed model (or, without one, the heuristic) picks. */
+/* (Learned schedule: this library's own, not a routine of the paper's
+ * runtime.)  Features (16 floats) the cost model sees for a loop, and the
+ * configuration index the installed model (or, without one, the heuristic)
+ * picks, for the loop the runtime divides (Sec. 2).  Host pointers; NULL ctx
+ * is OMPRT_ERR_NOT_INIT, a NULL output OMPRT_ERR_INVALID.  omprt_loop_features
+ * returns the trip count's error for a bad descriptor; omprt_choose_config
+ * reads the descriptor only when a model is installed (without one it returns
+ * the heuristic's index, and a launch validates the descriptor itself). */
 omprt_status omprt_loop_features(const omprt_ctx *ctx, const omprt_loop_desc *desc,
                                  int32_t has_reduction, float *features_host);
 omprt_status omprt_choose_config(const omprt_ctx *ctx, const omprt_loop_desc *desc,
