@@ -204,6 +204,19 @@ def test_owner_map_vs_brute():
         assert own.tolist() == brute_owner(n, G, T, c)
 
 
+def test_owner_map_vs_brute_random_larger():
+    """Seeded random launches well past the exhaustive range: thousands of
+    iterations, hundreds of teams, up to 1024 threads, chunks up to 300
+    (many threads and teams end up empty or with a partial last chunk)."""
+    rng = np.random.default_rng(11)
+    for _ in range(25):
+        n = int(rng.integers(0, 10000))
+        G = int(rng.integers(1, 300))
+        T = int(rng.choice([1, 32, 96, 256, 1024]))
+        c = int(rng.choice([0, 1, 2, 7, 64, 300]))
+        assert O.owner_map(n, G, T, c).tolist() == brute_owner(n, G, T, c), (n, G, T, c)
+
+
 @pytest.mark.parametrize("t,lb,incr", [("i64", 3, 2), ("i32", 50, -3), ("u64", 7, 1)])
 def test_composite_table_vs_brute(t, lb, incr):
     for n, G, T, c in itertools.product((0, 1, 5, 17, 40), (1, 2, 3, 5), (1, 4, 9),
@@ -259,6 +272,18 @@ def test_owner_map_dist_vs_brute():
     for n, G, T, d, c in itertools.product((0, 1, 7, 40, 97), (1, 2, 3, 5), (1, 3, 8),
                                            (1, 4, 8, 13), (0, 1, 3)):
         assert O.owner_map_dist(n, G, T, d, c).tolist() == brute_owner_dist(n, G, T, d, c)
+
+
+def test_owner_map_dist_vs_brute_random_larger():
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        n = int(rng.integers(0, 10000))
+        G = int(rng.integers(1, 200))
+        T = int(rng.choice([1, 32, 128, 512]))
+        d = int(rng.choice([1, T, 8 * T, 1000, 4099]))
+        c = int(rng.choice([0, 1, 3, 8, 64]))
+        assert O.owner_map_dist(n, G, T, d, c).tolist() == brute_owner_dist(n, G, T, d, c), \
+            (n, G, T, d, c)
 
 
 def test_owner_map_dist_spmd_closed_form():
