@@ -31,6 +31,7 @@ TYPE_CODES = {"i32": I32, "u32": U32, "i64": I64, "u64": U64}
 
 
 class OmprtError(RuntimeError):
+    """A non-OK omprt_status from the library; .status holds the code."""
     def __init__(self, status, what=""):
         self.status = status
         super().__init__("%s: %s (status %d)" % (what, status_str(status), status))
@@ -41,6 +42,7 @@ class LibraryMissing(RuntimeError):
 
 
 class LoopDesc(C.Structure):
+    """omprt_loop_desc (include/omprt.h): loop bounds, index type, body, data pointers."""
     _fields_ = [("lb", C.c_int64), ("ub", C.c_int64), ("incr", C.c_int64),
                 ("idx_type", C.c_int32), ("body", C.c_int32), ("data_type", C.c_int32),
                 ("reserved", C.c_int32), ("x", C.c_void_p), ("y", C.c_void_p),
@@ -49,6 +51,7 @@ class LoopDesc(C.Structure):
 
 
 class ReduceDesc(C.Structure):
+    """omprt_reduce_desc: reduction op, precision and the device result pointer."""
     _fields_ = [("op", C.c_int32), ("precision", C.c_int32), ("result_dev", C.c_void_p)]
 
 
@@ -100,6 +103,7 @@ def _declare(L):
 
 
 def lib_path():
+    """Path of the in-tree libomprt.so that lib() loads."""
     return build_lib.LIB
 
 
@@ -124,6 +128,7 @@ def loop_trip_count(desc):
 
 
 def status_str(s):
+    """omprt_status_str: the library's text for a status code."""
     try:
         return lib().omprt_status_str(s).decode()
     except OmprtError:
@@ -131,6 +136,7 @@ def status_str(s):
 
 
 def check(status, what="omprt"):
+    """Raise OmprtError unless status is OMPRT_OK."""
     if status != OK:
         raise OmprtError(status, what)
 
@@ -181,6 +187,7 @@ class Runtime:
         self.device = device
 
     def close(self):
+        """omprt_finalize: free the context (streams must be synchronised)."""
         if self.ctx:
             check(lib().omprt_finalize(self.ctx), "omprt_finalize")
             self.ctx = None
@@ -194,9 +201,11 @@ class Runtime:
 
     @property
     def sm_count(self):
+        """omprt_sm_count: SMs of the context's device."""
         return lib().omprt_sm_count(self.ctx)
 
     def alloc_shared(self, nbytes):
+        """omprt_alloc_shared: per-team shared-memory stack capacity for later launches."""
         check(lib().omprt_alloc_shared(self.ctx, int(nbytes)), "omprt_alloc_shared")
 
     def set_stage_bytes(self, nbytes):
@@ -205,6 +214,8 @@ class Runtime:
 
     def launch_region(self, desc, sched=SCHED_STATIC, chunk=0, teams=0, threads=0, red=None,
                       stream=None):
+        """omprt_launch_region: run desc's loop under sched / chunk on teams x threads
+        (0: defaults); red (ReduceDesc) adds a reduction.  Asynchronous on stream."""
         rd = None if red is None else C.byref(red)
         check(lib().omprt_launch_region(self.ctx, C.byref(desc), int(sched), int(chunk),
                                         int(teams), int(threads), rd, _stream(stream)),
@@ -212,6 +223,8 @@ class Runtime:
 
     def launch_region_dist(self, desc, dist_chunk, sched=SCHED_STATIC, chunk=0, teams=0,
                            threads=0, red=None, stream=None):
+        """omprt_launch_region_dist: dist_schedule(static, dist_chunk) at the team
+        level, sched / chunk inside each distribute chunk."""
         rd = None if red is None else C.byref(red)
         check(lib().omprt_launch_region_dist(self.ctx, C.byref(desc), int(dist_chunk), int(sched),
                                              int(chunk), int(teams), int(threads), rd,
@@ -226,12 +239,16 @@ class Runtime:
 
     def reduce(self, op, data, result, precision=PREC_COMP_F64, teams=0, threads=0, dtype=None,
                stream=None):
+        """omprt_reduce: reduction(op) over the device tensor data into result
+        (float64[1] for fp32 / bf16 data, int64[1] for integers)."""
         dt = _dtype_code(data) if dtype is None else dtype
         check(lib().omprt_reduce(self.ctx, int(op), int(dt), int(precision), _ptr(data),
                                  int(data.numel()), _ptr(result), int(teams), int(threads),
                                  _stream(stream)), "omprt_reduce")
 
     def static_init_table(self, desc, chunk, teams, threads, table, stream=None):
+        """omprt_static_init_table: table (int64 device tensor [G*T][8]) gets every
+        thread's static worksharing tuple."""
         check(lib().omprt_static_init_table(self.ctx, C.byref(desc), int(chunk), int(teams),
                                             int(threads), _ptr(table), _stream(stream)),
               "omprt_static_init_table")
@@ -246,18 +263,22 @@ class Runtime:
 
     # -- self-tests -------------------------------------------------------
     def test_atomics(self, teams, threads, reps, e, words, returned=None, stream=None):
+        """omprt_test_atomics: device self-test of the runtime atomics (tensors on device)."""
         check(lib().omprt_test_atomics(self.ctx, teams, threads, reps, e, _ptr(words),
                                        _ptr(returned), _stream(stream)), "omprt_test_atomics")
 
     def test_barrier(self, teams, threads, sub, rounds, errors, stream=None):
+        """omprt_test_barrier: device self-test of team and sub-team barriers."""
         check(lib().omprt_test_barrier(self.ctx, teams, threads, sub, rounds, _ptr(errors),
                                        _stream(stream)), "omprt_test_barrier")
 
     def test_wait(self, teams, flag, expect, timeout_us, out, stream=None):
+        """omprt_test_wait: bounded device wait on flag (device tensor); out[g] = seen."""
         check(lib().omprt_test_wait(self.ctx, teams, _ptr(flag), int(expect), int(timeout_us),
                                     _ptr(out), _stream(stream)), "omprt_test_wait")
 
     def test_stack(self, teams, stack_bytes, pool_bytes, ops, out, status, stream=None):
+        """omprt_test_stack: replay an alloc/free trace on the team stack (device tensors)."""
         nops = ops.shape[0] if ops is not None else 0
         check(lib().omprt_test_stack(self.ctx, teams, int(stack_bytes), int(pool_bytes),
                                      _ptr(ops), nops, _ptr(out), _ptr(status), _stream(stream)),
@@ -265,6 +286,7 @@ class Runtime:
 
     # -- batch ----------------------------------------------------------------
     def batch_create(self, descs, reds=None, chunk_elems=0):
+        """omprt_batch_create: a persistent batch of regions; returns a Batch."""
         n = len(descs)
         arr = (LoopDesc * n)(*descs)
         rarr = None if reds is None else (ReduceDesc * n)(*reds)
@@ -275,16 +297,19 @@ class Runtime:
 
     # -- MLP --------------------------------------------------------------------
     def mlp_forward(self, params, x, y, stream=None):
+        """omprt_mlp_forward: y[B][12] = model(x[B][16]) (device tensors)."""
         check(lib().omprt_mlp_forward(self.ctx, _ptr(params), _ptr(x), int(x.shape[0]), _ptr(y),
                                       _stream(stream)), "omprt_mlp_forward")
 
     def mlp_loss_grad(self, params, x, target, grad, loss=None, stream=None):
+        """omprt_mlp_loss_grad: grad = d loss / d params; loss[1] if given (device tensors)."""
         check(lib().omprt_mlp_loss_grad(self.ctx, _ptr(params), _ptr(x), _ptr(target),
                                         int(x.shape[0]), _ptr(grad), _ptr(loss),
                                         _stream(stream)), "omprt_mlp_loss_grad")
 
     def mlp_adam(self, params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
                  stream=None):
+        """omprt_mlp_adam: one bias-corrected Adam step on params (device tensors)."""
         check(lib().omprt_mlp_adam(self.ctx, _ptr(params), _ptr(grad), _ptr(m), _ptr(v),
                                    int(params.numel()), int(t), lr, beta1, beta2, eps,
                                    _stream(stream)), "omprt_mlp_adam")
@@ -302,6 +327,7 @@ class Runtime:
               "omprt_set_cost_model")
 
     def loop_features(self, desc, has_reduction):
+        """omprt_loop_features: the 16 features the cost model sees (numpy float32)."""
         import numpy as np
         f = np.zeros(MLP_IN, dtype=np.float32)
         check(lib().omprt_loop_features(self.ctx, C.byref(desc), int(bool(has_reduction)),
@@ -309,6 +335,7 @@ class Runtime:
         return f
 
     def choose_config(self, desc, has_reduction):
+        """omprt_choose_config: the configuration index the model (or heuristic) picks."""
         k = C.c_int32()
         check(lib().omprt_choose_config(self.ctx, C.byref(desc), int(bool(has_reduction)),
                                         C.byref(k)), "omprt_choose_config")
@@ -316,18 +343,22 @@ class Runtime:
 
 
 class Batch:
+    """A batch handle from Runtime.batch_create (omprt_batch)."""
     def __init__(self, handle):
         self.handle = handle
 
     @property
     def items(self):
+        """omprt_batch_items: work items (chunks) in the batch."""
         return lib().omprt_batch_items(self.handle)
 
     def launch(self, num_ctas=0, threads=0, stream=None):
+        """omprt_launch_batch: run every region in one persistent launch."""
         check(lib().omprt_launch_batch(self.handle, int(num_ctas), int(threads), _stream(stream)),
               "omprt_launch_batch")
 
     def destroy(self):
+        """omprt_batch_destroy: free the batch (streams must be synchronised)."""
         if self.handle:
             check(lib().omprt_batch_destroy(self.handle), "omprt_batch_destroy")
             self.handle = None
