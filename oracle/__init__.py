@@ -63,6 +63,8 @@ def _declare(L):
         "orc_exact_sum_f64": (dbl, [u64, vp]),
         "orc_exact_abs_sum_f32": (dbl, [u64, vp]),
         "orc_plain_sum_f32": (dbl, [u64, vp]),
+        "orc_exact_sum_f32_terms": (i32, [u64, vp, vp, i32]),
+        "orc_exact_sum_bf16_terms": (i32, [u64, vp, vp, i32]),
         "orc_atomic_inc": (C.c_uint32, [C.POINTER(C.c_uint32), C.c_uint32]),
         "orc_stack_replay": (i64, [u64, u64, u64, vp, vp]),
         "orc_mlp_nparam": (i32, []),
@@ -224,6 +226,21 @@ def exact_sum_f64(a):
 def exact_abs_sum_f32(a):
     a = np.ascontiguousarray(a, dtype=np.float32)
     return lib().orc_exact_abs_sum_f32(a.size, _p(a))
+
+
+def exact_sum_terms(a, bf16=False, cap=16):
+    """The exact sum of a (fp32 values, or bf16 patterns when bf16) as a
+    non-overlapping expansion of doubles, largest first."""
+    out = np.zeros(cap)
+    if bf16:
+        a = np.ascontiguousarray(a, dtype=np.uint16)
+        k = lib().orc_exact_sum_bf16_terms(a.size, _p(a), _p(out), cap)
+    else:
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        k = lib().orc_exact_sum_f32_terms(a.size, _p(a), _p(out), cap)
+    if k > cap:
+        raise OracleError("expansion longer than %d terms" % cap)
+    return out[:k].copy()
 
 
 def plain_sum_f32(a):

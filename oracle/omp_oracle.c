@@ -530,7 +530,50 @@ double orc_exact_abs_sum_f32(uint64_t n, const float *a)
     return kl_round(&acc);
 }
 
-/* Plain FP64 left-to-right loop: a speed reference, not an oracle. */
+/* The exact sum held in an accumulator as a non-overlapping expansion:
+ * t_1 = the sum rounded to the nearest double, t_2 = what is left rounded,
+ * and so on until nothing is left (each term takes 53 bits off the rest, so a
+ * sum of fp32 or bf16 values needs a handful).  Writes at most cap terms and
+ * returns how many the sum needs.  The terms of disjoint slices, summed by
+ * orc_exact_sum_f64, give the exact sum of the whole rounded once: slices can
+ * be summed on separate cores without losing exactness. */
+static int kl_terms(orc_kulisch *acc, double *out, int cap)
+{
+    int k = 0;
+    for (;;) {
+        orc_kulisch tmp = *acc;                 /* kl_round rewrites its argument */
+        double r = kl_round(&tmp);
+        if (r == 0.0) return k;
+        if (k < cap) out[k] = r;
+        k++;
+        kl_add(acc, -r);                        /* exact: r is a sum of addend bits */
+    }
+}
+
+int orc_exact_sum_f32_terms(uint64_t n, const float *a, double *out, int cap)
+{
+    orc_kulisch acc;
+    kl_init(&acc);
+    for (uint64_t i = 0; i < n; i++) kl_add(&acc, (double)a[i]);
+    return kl_terms(&acc, out, cap);
+}
+
+int orc_exact_sum_bf16_terms(uint64_t n, const uint16_t *a, double *out, int cap)
+{
+    orc_kulisch acc;
+    kl_init(&acc);
+    for (uint64_t i = 0; i < n; i++) {
+        uint32_t bits = (uint32_t)a[i] << 16;
+        float f;
+        memcpy(&f, &bits, 4);
+        kl_add(&acc, (double)f);
+    }
+    return kl_terms(&acc, out, cap);
+}
+
+/* Plain FP64 left-to-right loop (each fp32 value widened exactly, one fp64
+ * rounding per add): the CPU speed reference of the reduction configuration,
+ * not the oracle of a GPU result. */
 double orc_plain_sum_f32(uint64_t n, const float *a)
 {
     double s = 0.0;

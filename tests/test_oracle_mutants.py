@@ -92,8 +92,21 @@ MUTANTS = [
     ("exact_add_sign_of_top_digit", "if (v < 0) { d0 = -d0; d1 = -d1; d2 = -d2; }",
      "if (v < 0) { d0 = -d0; d1 = -d1; }"),
     ("exact_round_drops_sign", "return neg ? -r : r;", "return r;"),
+    ("plain_sum_fp32_accumulator", "double s = 0.0;\n    for (uint64_t i = 0; i < n; i++) s += (double)a[i];",
+     "float s = 0.0f;\n    for (uint64_t i = 0; i < n; i++) s += a[i];"),
+    ("plain_sum_right_to_left", "for (uint64_t i = 0; i < n; i++) s += (double)a[i];\n    return s;",
+     "for (uint64_t i = n; i > 0; i--) s += (double)a[i - 1];\n    return s;"),
+    ("plain_sum_drops_last", "for (uint64_t i = 0; i < n; i++) s += (double)a[i];\n    return s;",
+     "for (uint64_t i = 0; i + 1 < n; i++) s += (double)a[i];\n    return s;"),
+    ("exact_terms_first_only", "        kl_add(acc, -r);                        /* exact: r is a sum of addend bits */",
+     "        return k;"),
+    ("exact_terms_bf16_decode",
+     "uint32_t bits = (uint32_t)a[i] << 16;\n        float f;\n        memcpy(&f, &bits, 4);\n        kl_add(&acc, (double)f);\n    }\n    return kl_terms",
+     "uint32_t bits = (uint32_t)a[i] << 16;\n        float f;\n        memcpy(&f, &bits, 4);\n        kl_add(&acc, (double)f + 1.0);\n    }\n    return kl_terms"),
     ("abs_sum_without_abs", "kl_add(&acc, fabs((double)a[i]));", "kl_add(&acc, (double)a[i]);"),
-    ("bf16_decode_shift", "uint32_t bits = (uint32_t)a[i] << 16;", "uint32_t bits = (uint32_t)a[i] << 15;"),
+    ("bf16_decode_shift",
+     "double orc_exact_sum_bf16(uint64_t n, const uint16_t *a)\n{\n    orc_kulisch acc;\n    kl_init(&acc);\n    for (uint64_t i = 0; i < n; i++) {\n        uint32_t bits = (uint32_t)a[i] << 16;",
+     "double orc_exact_sum_bf16(uint64_t n, const uint16_t *a)\n{\n    orc_kulisch acc;\n    kl_init(&acc);\n    for (uint64_t i = 0; i < n; i++) {\n        uint32_t bits = (uint32_t)a[i] << 15;"),
     ("dot_transposed_operand", "kl_add(&acc, (double)x[i] * (double)y[i]);",
      "kl_add(&acc, (double)x[i] * (double)x[i]);"),
     # C8 atomic inc

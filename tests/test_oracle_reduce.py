@@ -146,3 +146,57 @@ def test_max_min_one_sided_single_and_empty():
     assert O.max_min(one, "max") == -3.5 and O.max_min(one, "min") == -3.5
     empty = np.zeros(0, np.float32)
     assert O.max_min(empty, "max") == float("-inf") and O.max_min(empty, "min") == float("inf")
+
+
+def test_plain_sum_pins():
+    """The plain fp64 loop (the CPU speed reference for the reductions, not the
+    oracle of a GPU result): left to right, each fp32 value widened exactly
+    and added with one fp64 rounding.
+    * Integer-valued data whose partial sums stay below 2^53 are summed
+      exactly, so the result equals the correctly rounded sum (math.fsum).
+    * Order: [2^54, -2^54, 1, 1, 1] is 3 left to right; right to left the
+      partial 3 - 2^54 rounds to 4 - 2^54 (spacing 2, ties to even) and the
+      result is 4.
+    * Accumulator width: [1, 1, 1, 1, 2^54, -2^54] is 4 in fp64 (2^54 + 4 is a
+      double); an fp32 accumulator would round 2^54 + 4 to 2^54 and return 0.
+    * Error bound of recursive summation: |plain - exact| <= (n - 1) u sum|x|
+      with u = 2^-53 (first order in n u, n u << 1 here)."""
+    f = np.float32
+    a = np.arange(-5000, 7000, 3, dtype=f)
+    assert O.plain_sum_f32(a) == fsum32(a)
+    assert O.plain_sum_f32(np.array([2.0 ** 54, -2.0 ** 54, 1, 1, 1], f)) == 3.0
+    assert O.plain_sum_f32(np.array([1, 1, 1, 1, 2.0 ** 54, -2.0 ** 54], f)) == 4.0
+    assert O.plain_sum_f32(np.array([], f)) == 0.0
+    for gen in (inputs.f32_uniform_pm1, inputs.f32_lognormal_signed):
+        x = gen(100000, 21)
+        err = abs(O.plain_sum_f32(x) - O.exact_sum_f32(x))
+        assert err <= (x.size - 1) * 2.0 ** -53 * O.exact_abs_sum_f32(x)
+
+
+def test_exact_sum_terms_split_across_slices():
+    """The expansion of each slice's exact sum: its terms add up exactly
+    (math.fsum) to the slice's correctly rounded sum's exact value, the first
+    term is that rounded sum, terms do not overlap (each below half an ulp
+    of the one before), and the terms of disjoint slices summed by the
+    oracle's exact fp64 sum give the whole array's exact sum."""
+    for gen, bf in ((inputs.f32_lognormal_signed, False), (inputs.f32_uniform_pm1, False),
+                    (inputs.bf16_uniform_pm1, True)):
+        a = gen(200003, 23)
+        whole = O.exact_sum_bf16(a) if bf else O.exact_sum_f32(a)
+        vals = (a.astype(np.uint32) << 16).view(np.float32) if bf else a
+        cuts = [0, 1, 5000, 77777, 150000, a.size]
+        terms = []
+        for lo, hi in zip(cuts[:-1], cuts[1:]):
+            t = O.exact_sum_terms(a[lo:hi], bf16=bf)
+            assert t.size >= 1
+            assert t[0] == fsum32(vals[lo:hi])
+            for u, v in zip(t[:-1], t[1:]):
+                assert abs(v) <= math.ulp(u) / 2
+            terms.extend(t.tolist())
+        assert O.exact_sum_f64(np.array(terms)) == whole
+        assert math.fsum(terms) == whole
+    # a sum that needs more than one term: 1 + 2^-60 (fp32 values)
+    t = O.exact_sum_terms(np.array([1.0, 2.0 ** -60], np.float32))
+    assert t.tolist() == [1.0, 2.0 ** -60]
+    assert O.exact_sum_terms(np.array([], np.float32)).size == 0
+    assert O.exact_sum_terms(np.array([3.0, -3.0], np.float32)).size == 0
