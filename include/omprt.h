@@ -151,6 +151,11 @@ typedef struct {
     double alpha;              /* AXPY scale (rounded to fp32 or int32) */
     double c0, c1;             /* stencil weights (rounded to fp32) */
     int64_t nx, ny;            /* STENCIL2D5 grid */
+    int32_t *seq;              /* MAP_RECORD only (NULL: skipped): int32[n];
+                                  seq[i] = how many iterations the thread that
+                                  ran i had run before it in this launch, so a
+                                  thread's iterations sorted by seq are in the
+                                  order it ran them.  Other bodies: NULL. */
 } omprt_loop_desc;
 
 /* reduction(op: var) clause of a region.  result_dev: 8 bytes of device
@@ -211,6 +216,25 @@ omprt_status omprt_alloc_shared(omprt_ctx *ctx, size_t bytes_per_team);
  * init: 32 KiB. */
 omprt_status omprt_set_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_team);
 
+/* Shared memory per CTA that the 2-D stencil (fp32, no reduction) may use
+ * under static, static(c) and dynamic(c) to stage its input.  Each team's
+ * block of the collapsed loop, plus one grid row on each side, is copied into
+ * shared memory by one bulk copy (the team-shared state of Sec. 3.1, "Global
+ * Shared Variables"), and every thread then runs exactly the iterations the
+ * schedule gives it (Sec. 1, Sec. 2 worksharing), reading its operands there.
+ * Dynamic chunks are claimed from the team's counter in shared memory, 32 per
+ * warp, lane l running chunk base + l; a thread's claims increase.  A launch
+ * has at most as many CTAs as fit the device at once; CTA k plays the
+ * consecutive teams [k G / P, (k + 1) G / P) in turn, in passes of whole teams
+ * whose two windows alternate (the next pass's copy in flight while one
+ * computes).  The form applies when nx is a multiple of 4, n < 2^32, both
+ * pointers are 16-byte aligned and two windows of one team (its block plus
+ * two rows) fit `bytes` and the device's per-block shared memory; other
+ * launches run the forms of omprt_set_stage_bytes.  bytes is rounded down to
+ * 16; 0 turns this form off; more than the device's per-block shared memory is
+ * OMPRT_ERR_INVALID.  Default after init: 192 KiB. */
+omprt_status omprt_set_stencil_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_cta);
+
 /*
  * Run one "target teams distribute parallel for" region:
  *   level 1: the n logical iterations are split among num_teams teams in
@@ -248,23 +272,41 @@ omprt_status omprt_launch_region_dist(omprt_ctx *ctx, const omprt_loop_desc *des
                                       int32_t num_teams, int32_t thread_limit,
                                       const omprt_reduce_desc *red, void *stream);
 
-/* Generic-mode (non-SPMD) region over segments (the runtime's main-thread /
- * worker state machine and __kmpc_alloc_shared for variables the sequential
- * code shares with a parallel region, Sec. 2.1, Listing 1):
- *   teams distribute (static, balanced) over the nseg segments; for each of
- *   its segments s the team's main thread globalises a double v = 0 on the
- *   team stack, hands the parallel region to the team, all threads run
- *   parallel for (static) over [seg_dev[s], seg_dev[s+1]) with
- *   reduction(+: v), and after the join the main thread stores
- *   result_dev[s] = v and releases v.
- * desc: body DOT (v = sum x[i]*y[i]) or AXPY (y[i] = alpha*x[i] + y[i],
- * v = sum of the new y[i]), data_type F32; its trip count n bounds the
- * offsets (0 <= seg_dev[s] <= seg_dev[s+1] <= n, else the team stops and
- * OMPRT_DEV_BAD_ARG is set).  seg_dev: int64[nseg + 1] device; result_dev:
- * double[nseg] device.  num_teams 0 = SMs; thread_limit 0 = 256. */
+/* Generic-mode (non-SPMD) regions over segments: the runtime's main-thread /
+ * worker state machine and __kmpc_alloc_shared for the variables the
+ * sequential code shares with its parallel regions (Sec. 2.1, Listing 1).
+ * teams distribute (static, balanced) over the nseg segments; for each of its
+ * segments s = [seg_dev[s], seg_dev[s+1]) the team's main thread (thread 0)
+ * runs the sequential code of `program`, and for each parallel region in it
+ * publishes a work descriptor in team-shared memory (the outlined region's
+ * id, its loop bounds, its arguments: the scale and a pointer to the
+ * globalised reduction variable) and releases the waiting workers; every
+ * thread dispatches on the id and runs the region's parallel for (the
+ * default schedule: static with a chunk of one 32-byte vector) with a
+ * compensated reduction into the variable; a join barrier returns control to
+ * the main thread.  Globalised variables live on the team stack of capacity
+ * S (omprt_alloc_shared), overflowing to the team's 4 KiB pool slice (teams
+ * below OMPRT_MAX_RED_TEAMS); a request that does not fit sets
+ * OMPRT_DEV_STACK_NOMEM and the team stops (its remaining results are not
+ * written).
+ *   OMPRT_GENERIC_REDUCE: one region per segment, v = 0;
+ *     parallel for reduction(+: v) with desc's body: DOT v += x[i]*y[i], or
+ *     AXPY y[i] = alpha*x[i] + y[i], v += y[i]; result_dev[s] = v.
+ *   OMPRT_GENERIC_DOT_AXPY: two regions per segment, the second using the
+ *     first's result: v = sum x[i]*y[i] (region 1); a = (float)v * alpha
+ *     (sequential, fp32 product); y[i] = a*x[i] + y[i] with w = sum of the
+ *     new y[i] (region 2); result_dev[3s .. 3s+2] = v, a, w.
+ * desc: data_type F32, x / y device arrays of its trip count n, which bounds
+ * the offsets (0 <= seg_dev[s] <= seg_dev[s+1] <= n, else the team stops and
+ * OMPRT_DEV_BAD_ARG is set); alpha as above.  seg_dev: int64[nseg + 1] device;
+ * result_dev: double[nseg] or double[3 nseg] device.  num_teams 0 = SMs;
+ * thread_limit 0 = 256. */
+#define OMPRT_GENERIC_REDUCE 0
+#define OMPRT_GENERIC_DOT_AXPY 1
 omprt_status omprt_launch_generic(omprt_ctx *ctx, const int64_t *seg_dev, int64_t nseg,
-                                  const omprt_loop_desc *desc, double *result_dev,
-                                  int32_t num_teams, int32_t thread_limit, void *stream);
+                                  const omprt_loop_desc *desc, int32_t program,
+                                  double *result_dev, int32_t num_teams, int32_t thread_limit,
+                                  void *stream);
 
 /* reduction(op) over n elements of dtype (F32, BF16, I32, I64) at data_dev:
  * omprt_launch_region with BODY_NONE and schedule AUTO, the reduction clause of
@@ -314,12 +356,11 @@ int32_t omprt_sm_count(const omprt_ctx *ctx);
 /* ------------------------------------------------------------------ */
 /* Reduction without any allocation                                    */
 /* ------------------------------------------------------------------ */
-/* The paper has no counterpart to this call (it is a reduction clause over
- * the loop the runtime divides, Sec. 2, like omprt_reduce); it exists for callers of this
- * library that cannot allocate device memory: code running while a CUDA
- * graph is being captured, inside a stream callback or an allocator hook,
- * under a lock that cudaMalloc could need, or in a process whose device
- * memory is owned and budgeted by another component.  It needs no context.
+/* The paper has no counterpart to this call.  It exists for callers of this
+ * library that cannot allocate device memory: code inside a stream callback
+ * or an allocator hook, code holding a lock that cudaMalloc could need, or a
+ * process whose device memory is owned and budgeted by another component.
+ * It needs no context.
  *
  * Same operation and arguments as omprt_reduce (AUTO mapping, value body),
  * but the per-team partials and the ticket live in one scratch array
@@ -330,15 +371,19 @@ int32_t omprt_sm_count(const omprt_ctx *ctx);
  * means 512.  The call never calls cudaMalloc, cudaFree or any allocating
  * routine.
  *  - The first call on a device looks up the array's device address for
- *    that device (cudaGetSymbolAddress, with that device current); make that
- *    first call before any stream capture.
+ *    that device (cudaGetSymbolAddress, with that device current) and keeps
+ *    it for the life of the process; make that first call before any stream
+ *    capture.  The kept address is invalid after cudaDeviceReset on that
+ *    device: do not call this entry point after such a reset.
  *  - Every call shares the one array and clears its ticket on `stream`
  *    before launching, so calls that overlap on the GPU (different streams,
  *    or the same scratch used by two graphs running at once) race and give
  *    wrong results.  Calls ordered on one stream are safe.
  *  - The array keeps the last call's partials; nothing reads them later.
- *  - No device status word is reported: the team stack is fixed at 4 KiB,
- *    which always holds the call's 512 bytes of temporaries. */
+ *  - No device status word is reported, and none is needed: the team stack
+ *    is fixed at 4 KiB, which always holds the call's 512 bytes of
+ *    temporaries (checked when the library is compiled), and the value loop
+ *    has no bounded waits. */
 #define OMPRT_NOALLOC_MAX_TEAMS 4096
 omprt_status omprt_reduce_noalloc(int32_t op, int32_t dtype, int32_t precision,
                                   const void *data_dev, int64_t n, void *result_dev,

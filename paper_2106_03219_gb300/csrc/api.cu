@@ -17,6 +17,8 @@ constexpr size_t kPartialBytes = 16ull * OMPRT_MAX_RED_TEAMS;
 constexpr size_t kDynBytes = 8ull * OMPRT_MAX_RED_TEAMS;
 constexpr size_t kSlotBytes = kTicketBytes + kPartialBytes + kDynBytes;
 constexpr uint32_t kMaxStackBytes = 200u * 1024u;
+// shared memory per CTA for the staged 2-D stencil windows (two windows)
+constexpr uint32_t kStencilStageDefault = 192u * 1024u;
 
 bool is_int_type(int32_t t) { return t >= OMPRT_I32 && t <= OMPRT_U64; }
 
@@ -76,6 +78,7 @@ omprt_status loop_trip_count(const omprt_loop_desc* d, uint64_t* n, int64_t* wid
 
 static omprt_status validate_body(const omprt_loop_desc* d, uint64_t n) {
   if (d->reserved != 0) return OMPRT_ERR_INVALID;
+  if (d->seq && d->body != OMPRT_BODY_MAP_RECORD) return OMPRT_ERR_INVALID;
   switch (d->body) {
     case OMPRT_BODY_MAP_RECORD:
       if (!d->out && n) return OMPRT_ERR_INVALID;
@@ -180,6 +183,7 @@ omprt_status omprt_init(int device, omprt_ctx** out) {
   cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, device);
   cudaDeviceGetAttribute(&c->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   c->stack_bytes = 4096;
+  c->stencil_stage_bytes = kStencilStageDefault;
   bool ok = cudaMalloc(&c->status_dev, 256) == cudaSuccess &&
             cudaMalloc(&c->slots_dev, kSlotBytes * OMPRT_SLOTS) == cudaSuccess &&
             cudaMalloc(&c->pool_dev, (size_t)OMPRT_MAX_RED_TEAMS * OMPRT_POOL_BYTES_PER_TEAM) ==
@@ -227,6 +231,13 @@ omprt_status omprt_set_stage_bytes(omprt_ctx* c, int64_t bytes) {
   if (!c) return OMPRT_ERR_NOT_INIT;
   if (bytes < 0 || bytes > (int64_t)c->max_smem_optin) return OMPRT_ERR_INVALID;
   c->stage_bytes = (uint32_t)(bytes & ~int64_t(15));
+  return OMPRT_OK;
+}
+
+omprt_status omprt_set_stencil_stage_bytes(omprt_ctx* c, int64_t bytes) {
+  if (!c) return OMPRT_ERR_NOT_INIT;
+  if (bytes < 0 || bytes > (int64_t)c->max_smem_optin) return OMPRT_ERR_INVALID;
+  c->stencil_stage_bytes = (uint32_t)(bytes & ~int64_t(15));
   return OMPRT_OK;
 }
 
@@ -379,6 +390,7 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
   a.x = d->x;
   a.y = d->y;
   a.out = d->out;
+  a.seq = d->seq;
   a.alpha_f = (float)d->alpha;
   a.alpha_i = d->data_type == OMPRT_I32 ? (int32_t)d->alpha : 0;
   a.c0 = (float)d->c0;
@@ -426,6 +438,16 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
     e = launch_stencil2d_tiles(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny,
                                (float)d->c0, (float)d->c1, (unsigned)teams, (unsigned)threads,
                                c->status_dev, st);
+    if (e != cudaErrorNotSupported) return from_cuda(e);
+    cudaGetLastError();
+  }
+  if (d->body == OMPRT_BODY_STENCIL2D5 && acc == kAccNone && d->data_type == OMPRT_F32 &&
+      (ksched == kStatic || ksched == kChunked || ksched == kDynamic) &&
+      c->stencil_stage_bytes != 0) {
+    e = launch_stencil2d_owner(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny, ksched,
+                               (uint64_t)chunk, (float)d->c0, (float)d->c1, (unsigned)teams,
+                               (unsigned)threads, c->stencil_stage_bytes, c->sm_count,
+                               c->max_smem_optin, c->status_dev, st);
     if (e != cudaErrorNotSupported) return from_cuda(e);
     cudaGetLastError();
   }

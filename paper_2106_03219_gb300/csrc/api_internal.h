@@ -18,6 +18,7 @@ struct omprt_ctx {
   float* mlp_rows_dev = nullptr;   // MLP per-sample scratch, kMlpMaxBatch rows
   uint32_t stack_bytes = 0;
   uint32_t stage_bytes = 32768;    // per-team shared memory for staged dynamic schedules
+  uint32_t stencil_stage_bytes = 0;  // per-CTA shared memory for the staged 2-D stencil windows
   std::atomic<uint32_t> next_slot{0};
   // learned schedule (host copy of the model)
   bool has_model = false;

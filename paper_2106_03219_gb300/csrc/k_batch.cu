@@ -186,7 +186,8 @@ omprt_status omprt_batch_create(omprt_ctx* c, const omprt_loop_desc* descs,
     int64_t lb;
     omprt_status s = loop_trip_count(&d, &n, &lb);
     if (s) return s;
-    if (d.lb != 0 || d.incr != 1 || d.data_type != OMPRT_F32 || d.reserved) return OMPRT_ERR_INVALID;
+    if (d.lb != 0 || d.incr != 1 || d.data_type != OMPRT_F32 || d.reserved || d.seq)
+      return OMPRT_ERR_INVALID;
     const bool red = reds && reds[r].result_dev;
     if (red && (reds[r].op != OMPRT_OP_SUM || reds[r].precision != OMPRT_PREC_COMP_F64))
       return OMPRT_ERR_UNSUPPORTED;

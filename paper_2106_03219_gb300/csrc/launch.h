@@ -48,6 +48,15 @@ cudaError_t launch_stencil2d_rows(const void* in, float* out, uint64_t nx, uint6
                                   unsigned threads, int max_smem, uint32_t* status,
                                   cudaStream_t st);
 
+// static, static(c) and dynamic(c) 2-D stencil with each team's rows staged
+// in shared memory by bulk copies, `budget` bytes per CTA
+// (k_stencil_owner.cu); cudaErrorNotSupported (nothing launched) where that
+// form does not apply.
+cudaError_t launch_stencil2d_owner(const void* in, float* out, uint64_t nx, uint64_t ny, int sched,
+                                   uint64_t chunk, float c0, float c1, unsigned teams,
+                                   unsigned threads, uint32_t budget, int sm_count, int max_smem,
+                                   uint32_t* status, cudaStream_t st);
+
 // Support kernels (k_support.cu).
 cudaError_t launch_static_table(uint64_t n, int64_t lb, int64_t incr, uint64_t chunk, unsigned G,
                                 unsigned T, int64_t* table, cudaStream_t st);

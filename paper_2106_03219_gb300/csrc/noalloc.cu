@@ -1,12 +1,12 @@
 // A reduction entry point that allocates nothing: its cross-team scratch is a
 // fixed array compiled into the library instead of memory from a context.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA-graph
-// capture, a host callback or an allocator hook, code holding a lock that an
-// allocation would take, or code running in a process whose device memory is
-// owned and budgeted by someone else.  omprt_reduce_noalloc serves them.  It
-// runs the same reduction kernel as omprt_reduce; only the place the kernel
-// keeps its per-team partials and its ticket differs.
+// Some callers cannot call cudaMalloc: code in a host callback or an
+// allocator hook, code holding a lock that an allocation could need, or code
+// running in a process whose device memory is owned and budgeted by someone
+// else.  omprt_reduce_noalloc serves them.  It runs the same reduction kernel
+// as omprt_reduce; only the place the kernel keeps its per-team partials and
+// its ticket differs.
 #include <cstring>
 #include <mutex>
 
@@ -21,6 +21,13 @@ namespace {
 constexpr size_t kHeaderBytes = 256;
 constexpr uint32_t kNoallocStackBytes = 4096;  // team stack (dynamic shared memory)
 constexpr size_t kScratchBytes = kHeaderBytes + 16ull * OMPRT_NOALLOC_MAX_TEAMS;
+// The only device-side error this path could raise is a team stack too small
+// for the reduction's temporary (32 per-warp partials of at most 16 bytes,
+// taken by the epilogue with team_alloc; the stack's bookkeeping lives in
+// static shared memory).  With this capacity that allocation always
+// succeeds, and the AUTO value loop has no waits, so the status word below
+// is never set.
+static_assert(kNoallocStackBytes >= 32 * 16, "noalloc team stack holds the reduction temporary");
 
 static __device__ __align__(256) unsigned char noalloc_scratch[kScratchBytes];
 
@@ -79,7 +86,9 @@ extern "C" omprt_status omprt_reduce_noalloc(int32_t op, int32_t dtype, int32_t 
   omprt_status s = scratch_for_current_device(&scratch);
   if (s) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  // the ticket must start at zero: clear it (and the status word) in stream order
+  // A completed launch leaves its ticket at 0 (atomicInc(ticket, G - 1) wraps
+  // on the last team); this clear, in stream order, only repairs a ticket (and
+  // status word) left behind by a launch that did not run to the end.
   if (cudaMemsetAsync(scratch, 0, 8, st) != cudaSuccess) {
     cudaGetLastError();
     return OMPRT_ERR_CUDA;

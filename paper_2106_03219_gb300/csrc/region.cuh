@@ -38,6 +38,7 @@ struct RegionArgs {
   const void* x;
   void* y;
   void* out;
+  int32_t* seq;     // map record: per-iteration ordinal within its thread (may be null)
   float alpha_f;
   int32_t alpha_i;
   float c0, c1;     // stencil weights
@@ -73,9 +74,12 @@ struct BodyMapRecord {
   int32_t* owner;
   int32_t* count;
   int32_t* last;
+  int32_t* seq;
   int32_t id;
+  mutable int32_t ord;  // iterations this thread has run so far
   __device__ explicit BodyMapRecord(const RegionArgs& a)
-      : owner((int32_t*)a.out), count((int32_t*)a.y), last((int32_t*)a.x), id(0) {}
+      : owner((int32_t*)a.out), count((int32_t*)a.y), last((int32_t*)a.x), seq(a.seq), id(0),
+        ord(0) {}
   __device__ bool vec_ok() const { return false; }
   struct S1 {};
   __device__ __forceinline__ void load1(uint64_t, S1&) const {}
@@ -83,6 +87,7 @@ struct BodyMapRecord {
   __device__ __forceinline__ void finish1(uint64_t i, const S1&, Acc&) const {
     owner[i] = id;
     if (count) atomicAdd(count + i, 1);
+    if (seq) seq[i] = ord++;
   }
   template <bool kN = false>
   __device__ void load(uint64_t, Frag&) const {}

@@ -208,6 +208,60 @@ def evaluate(rt, model, kind, n, T, buf):
             "decision_us": decide_us}
 
 
+def compare_picks(rt, model, kind, n, buf, reps=5, rounds=3, seed=0):
+    """The model's pick against the heuristic's on the same loops, timed
+    interleaved: for every loop, `reps` launches of the model's configuration
+    alternate with `reps` of the heuristic's (CUDA events around each), and
+    the loop's time under each is the median of its reps.  The whole set is
+    timed `rounds` times, each in a fresh random loop order.  Returns the
+    total time of each pick per round, the gain heuristic / model per round,
+    and its mean and spread (sample standard deviation and range)."""
+    import torch
+    cfgs = R.learned_configs()
+    sms = rt.sm_count
+    model.install(rt)
+    descs, picks = [], []
+    try:
+        for k, m in zip(kind, n):
+            d, red = loop_desc(int(k), int(m), buf)
+            descs.append((d, red))
+            picks.append(rt.choose_config(d, red is not None))
+    finally:
+        rt.set_cost_model(None)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * reps + 1)]
+    rng = np.random.default_rng(seed)
+    tot_model, tot_heur = [], []
+    for _ in range(rounds):
+        tm = th = 0.0
+        for i in rng.permutation(len(descs)):
+            d, red = descs[i]
+            run = [cfgs[picks[i]], cfgs[HEURISTIC]]
+            for sched, chunk, tps, thr in run:  # warm both
+                rt.launch_region(d, sched, chunk, tps * sms, thr, red=red, stream=stream)
+            j = 0
+            ev[0].record(stream)
+            for _r in range(reps):
+                for sched, chunk, tps, thr in run:
+                    rt.launch_region(d, sched, chunk, tps * sms, thr, red=red, stream=stream)
+                    j += 1
+                    ev[j].record(stream)
+            ev[j].synchronize()
+            t = [ev[q].elapsed_time(ev[q + 1]) for q in range(j)]
+            tm += float(np.median(t[0::2]))
+            th += float(np.median(t[1::2]))
+        tot_model.append(tm)
+        tot_heur.append(th)
+    assert rt.sync_status() == 0
+    gain = [h / m for h, m in zip(tot_heur, tot_model)]
+    return {"loops": len(descs), "reps": reps, "rounds": rounds,
+            "model_total_ms": tot_model, "heuristic_total_ms": tot_heur,
+            "gain_per_round": gain, "gain_mean": float(np.mean(gain)),
+            "gain_std": float(np.std(gain, ddof=1)) if rounds > 1 else 0.0,
+            "gain_range": [float(min(gain)), float(max(gain))],
+            "loops_model_differs": int(sum(1 for p in picks if p != HEURISTIC))}
+
+
 def main():
     import argparse
     import torch

@@ -26,6 +26,7 @@ MAX_RED_TEAMS = 16384
 POOL_BYTES_PER_TEAM = 4096
 MLP_IN, MLP_HID, MLP_OUT, MLP_NPARAM = 16, 64, 12, 6028
 NOALLOC_MAX_TEAMS = 4096
+GENERIC_REDUCE, GENERIC_DOT_AXPY = 0, 1
 
 TYPE_CODES = {"i32": I32, "u32": U32, "i64": I64, "u64": U64}
 
@@ -47,7 +48,8 @@ class LoopDesc(C.Structure):
                 ("idx_type", C.c_int32), ("body", C.c_int32), ("data_type", C.c_int32),
                 ("reserved", C.c_int32), ("x", C.c_void_p), ("y", C.c_void_p),
                 ("out", C.c_void_p), ("alpha", C.c_double), ("c0", C.c_double),
-                ("c1", C.c_double), ("nx", C.c_int64), ("ny", C.c_int64)]
+                ("c1", C.c_double), ("nx", C.c_int64), ("ny", C.c_int64),
+                ("seq", C.c_void_p)]
 
 
 class ReduceDesc(C.Structure):
@@ -66,11 +68,12 @@ def _declare(L):
         "omprt_finalize": (st, [vp]),
         "omprt_alloc_shared": (st, [vp, C.c_size_t]),
         "omprt_set_stage_bytes": (st, [vp, i64]),
+        "omprt_set_stencil_stage_bytes": (st, [vp, i64]),
         "omprt_launch_region": (st, [vp, C.POINTER(LoopDesc), i32, i64, i32, i32,
                                      C.POINTER(ReduceDesc), vp]),
         "omprt_launch_region_dist": (st, [vp, C.POINTER(LoopDesc), i64, i32, i64, i32, i32,
                                           C.POINTER(ReduceDesc), vp]),
-        "omprt_launch_generic": (st, [vp, vp, i64, C.POINTER(LoopDesc), vp, i32, i32, vp]),
+        "omprt_launch_generic": (st, [vp, vp, i64, C.POINTER(LoopDesc), i32, vp, i32, i32, vp]),
         "omprt_reduce": (st, [vp, i32, i32, i32, vp, i64, vp, i32, i32, vp]),
         "omprt_reduce_noalloc": (st, [i32, i32, i32, vp, i64, vp, i32, i32, vp]),
         "omprt_static_init_table": (st, [vp, C.POINTER(LoopDesc), i64, i32, i32, vp, vp]),
@@ -158,8 +161,9 @@ def _dtype_code(t):
 
 
 def loop_desc(body, n=None, x=None, y=None, out=None, *, lb=0, ub=None, incr=1, idx_type=I64,
-              data_type=None, alpha=3.0, c0=0.5, c1=0.125, nx=0, ny=0):
-    """Build an omprt_loop_desc.  Give either n (then lb=0, incr=1) or lb/ub/incr."""
+              data_type=None, alpha=3.0, c0=0.5, c1=0.125, nx=0, ny=0, seq=None):
+    """Build an omprt_loop_desc.  Give either n (then lb=0, incr=1) or lb/ub/incr.
+    seq (map record only): int32 device tensor of per-iteration ordinals."""
     if ub is None:
         ub = lb + (n - 1) * incr
     if data_type is None:
@@ -171,9 +175,9 @@ def loop_desc(body, n=None, x=None, y=None, out=None, *, lb=0, ub=None, incr=1, 
     d = LoopDesc(to64(lb_i), to64(ub_i), int(incr), int(idx_type), int(body), int(data_type), 0,
                  None if x is None else x.data_ptr(), None if y is None else y.data_ptr(),
                  None if out is None else out.data_ptr(), float(alpha), float(c0), float(c1),
-                 int(nx), int(ny))
+                 int(nx), int(ny), None if seq is None else seq.data_ptr())
     # the descriptor holds raw device pointers: keep the tensors alive with it
-    d._keep = (x, y, out)
+    d._keep = (x, y, out, seq)
     return d
 
 
@@ -212,6 +216,12 @@ class Runtime:
         """Per-team shared memory for staged dynamic schedules (0: plain form)."""
         check(lib().omprt_set_stage_bytes(self.ctx, int(nbytes)), "omprt_set_stage_bytes")
 
+    def set_stencil_stage_bytes(self, nbytes):
+        """omprt_set_stencil_stage_bytes: per-CTA shared memory for the staged 2-D
+        stencil windows under static / static(c) / dynamic(c) (0: off)."""
+        check(lib().omprt_set_stencil_stage_bytes(self.ctx, int(nbytes)),
+              "omprt_set_stencil_stage_bytes")
+
     def launch_region(self, desc, sched=SCHED_STATIC, chunk=0, teams=0, threads=0, red=None,
                       stream=None):
         """omprt_launch_region: run desc's loop under sched / chunk on teams x threads
@@ -230,12 +240,15 @@ class Runtime:
                                              int(chunk), int(teams), int(threads), rd,
                                              _stream(stream)), "omprt_launch_region_dist")
 
-    def launch_generic(self, seg, desc, result, teams=0, threads=0, stream=None):
-        """seg: int64 device tensor of nseg + 1 offsets; result: float64[nseg]."""
+    def launch_generic(self, seg, desc, result, teams=0, threads=0, stream=None,
+                       program=GENERIC_REDUCE):
+        """omprt_launch_generic: generic-mode regions over segments.  seg: int64
+        device tensor of nseg + 1 offsets; result: float64[nseg] (GENERIC_REDUCE)
+        or float64[3 * nseg] (GENERIC_DOT_AXPY: v, a, w per segment)."""
         nseg = max(int(seg.numel()) - 1, 0)
-        check(lib().omprt_launch_generic(self.ctx, _ptr(seg), nseg, C.byref(desc), _ptr(result),
-                                         int(teams), int(threads), _stream(stream)),
-              "omprt_launch_generic")
+        check(lib().omprt_launch_generic(self.ctx, _ptr(seg), nseg, C.byref(desc), int(program),
+                                         _ptr(result), int(teams), int(threads),
+                                         _stream(stream)), "omprt_launch_generic")
 
     def reduce(self, op, data, result, precision=PREC_COMP_F64, teams=0, threads=0, dtype=None,
                stream=None):

@@ -30,15 +30,30 @@ def test_static_init_table_bit_exact(rt, t, lb, incr):
                 assert np.array_equal(host(tab), ref), (n, G, T, c)
 
 
-def _map_record(rt, n, G, T, sched, chunk):
+def _map_record(rt, n, G, T, sched, chunk, with_seq=False):
     import torch
     owner = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
     count = torch.zeros((max(n, 1),), dtype=torch.int32, device="cuda")
     last = torch.full((G * T,), -1, dtype=torch.int32, device="cuda")
-    desc = R.loop_desc(R.BODY_MAP_RECORD, n=n, x=last, y=count, out=owner, data_type=R.I32)
+    seq = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda") if with_seq else None
+    desc = R.loop_desc(R.BODY_MAP_RECORD, n=n, x=last, y=count, out=owner, data_type=R.I32,
+                       seq=seq)
     rt.launch_region(desc, sched, chunk, G, T)
     assert rt.sync_status() == 0
+    if with_seq:
+        return host(owner)[:n], host(count)[:n], host(last), host(seq)[:n]
     return host(owner)[:n], host(count)[:n], host(last)
+
+
+def _run_order(owner, seq):
+    """Per thread: its iterations in the order it ran them (sorted by seq).
+    Checks that every thread's seq values are exactly 0 .. k-1."""
+    order = np.lexsort((seq, owner))          # by owner, then by seq
+    own, sq = owner[order], seq[order]
+    starts = np.flatnonzero(np.r_[True, own[1:] != own[:-1]])
+    rank = np.arange(owner.size) - np.repeat(starts, np.diff(np.r_[starts, owner.size]))
+    assert np.array_equal(sq, rank), "a thread's ordinals are not 0 .. k-1"
+    return order, own
 
 
 CASES = [(0, 4, 32), (1, 1, 32), (31, 4, 32), (1000, 13, 128), (100003, 148, 256),
@@ -60,11 +75,22 @@ def test_static_owner_map_bit_exact(rt, n, G, T, chunk):
 @pytest.mark.parametrize("n,G,T", CASES)
 @pytest.mark.parametrize("chunk", [1, 7, 256])
 def test_dynamic_invariants(rt, n, G, T, chunk):
-    owner, count, last = _map_record(rt, n, G, T, R.SCHED_DYNAMIC, chunk)
+    """C4: (1) every iteration runs exactly once; (2) each thread runs whole
+    chunks of its own team's block; (3) every thread runs its chunks, and the
+    iterations inside them, in increasing order (the claim counter only
+    grows); (4) the claims: team g's ceil(n_g / c) chunks are handed out in
+    groups of 32 consecutive chunks (one atomic add per warp), chunk j of a
+    group going to lane j mod 32 of one warp, so the team makes
+    ceil(ceil(n_g / c) / 32) warp claims that get work; (5) exactly one
+    thread is last."""
+    owner, count, last, seq = _map_record(rt, n, G, T, R.SCHED_DYNAMIC, chunk, with_seq=True)
     assert np.all(count == 1)                         # every iteration exactly once
     assert int((last == 1).sum()) == (1 if n else 0)  # exactly one thread is last
     if n:
         assert last[owner[n - 1]] == 1
+        order, own = _run_order(owner, seq)
+        same_thread = own[1:] == own[:-1]
+        assert np.all(np.diff(order)[same_thread] > 0)  # (3) increasing, per thread
     for g in range(G):
         bs, bn = O.static_nochunk(n, G, g)            # level 1 stays static
         blk = owner[bs:bs + bn]
@@ -72,6 +98,39 @@ def test_dynamic_invariants(rt, n, G, T, chunk):
         idx = np.arange(bn)
         same = (idx[1:] // chunk) == (idx[:-1] // chunk)   # neighbours in one chunk
         assert np.all(blk[1:][same] == blk[:-1][same])      # each chunk has one owner
+        if bn:
+            nch = (bn - 1) // chunk + 1
+            cown = blk[::chunk]                       # owner of each chunk
+            assert cown.size == nch                   # (4) ceil(n_g / c) chunk claims
+            j = np.arange(nch)
+            assert np.all((cown % T) % 32 == j % 32)  # lane j mod 32 runs chunk j
+            warp = (cown % T) // 32
+            grp = j // 32
+            first = np.r_[True, grp[1:] != grp[:-1]]
+            assert np.all(warp == np.repeat(warp[first], np.diff(np.r_[np.flatnonzero(first),
+                                                                       nch])))
+            assert int(first.sum()) == (nch + 31) // 32   # warp claims with work
+
+
+@pytest.mark.parametrize("n,G,T", [(1000, 13, 128), (100003, 148, 256), (5000, 3, 1024),
+                                   ((1 << 20) + 7, 64, 512)])
+@pytest.mark.parametrize("chunk", [1, 16, 256])
+def test_guided_claims_in_order_and_shrinking(rt, n, G, T, chunk):
+    """schedule(guided) is monotonic too: each thread runs its chunks in
+    increasing order, and along the team's block the chunk sizes never grow
+    except where the last chunk is cut short by the block's end."""
+    owner, count, last, seq = _map_record(rt, n, G, T, R.SCHED_GUIDED, chunk, with_seq=True)
+    assert np.all(count == 1)
+    order, own = _run_order(owner, seq)
+    assert np.all(np.diff(order)[own[1:] == own[:-1]] > 0)
+    for g in range(G):
+        bs, bn = O.static_nochunk(n, G, g)
+        starts = O.guided_chunks(bn, T, chunk)
+        sizes = np.diff(np.r_[starts, bn])
+        assert np.all(np.diff(sizes[:-1]) <= 0) if sizes.size > 2 else True
+        blk = owner[bs:bs + bn]
+        for a, e in zip(starts, np.r_[starts[1:], bn]):
+            assert np.all(blk[a:e] == blk[a])         # one owner per chunk
 
 
 @pytest.mark.parametrize("n,G,T", CASES)
