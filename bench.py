@@ -13,7 +13,10 @@ e2e       = the same bytes / time of a step through the C ABI with the inputs
 roofline  = the kernel with the largest share of the step: its algorithmic
             bytes per launch / its mean launch time, against the measured HBM
             copy bandwidth.
-cpu_baseline / --impl reference = the CPU oracle timed on a bounded sample.
+cpu_baseline / --impl reference = the CPU oracle on the same workload, on all
+            host cores (one slice per core) and on one core.
+kernels   = per-kernel event times inside the timed step; kernels_steady =
+            each kernel alone, back to back over rotating buffer copies.
 
 Launch: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference];
 for N > 1 under torch.distributed.run, every rank runs the same workload on
@@ -28,6 +31,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -166,62 +171,230 @@ def barrier(ws):
         dist.barrier()
 
 
-# -- CPU oracle leg ----------------------------------------------------------------
+# -- CPU oracle legs --------------------------------------------------------------------
+#
+# The oracle as it stands, on the host: on every host core (disjoint slices in
+# spawned worker processes, oracle/cores.py) and on one core.  These are
+# reported baselines, not targets.
 
-def oracle_sample_step(x, y, grid):
-    """One bounded sample of the step on the CPU oracle: axpy over x/y and the
+def oracle_step_one_core(x, y, grid):
+    """One worksharing step on one core: fp32 axpy over x / y and the 2-D
     stencil over grid, once per schedule (the oracle is sequential, so every
-    schedule runs the same loop).  Returns algorithmic bytes."""
+    schedule runs the same loop).  Returns (seconds, algorithmic bytes)."""
     import oracle as O
-    nbytes = 0
-    for _ in SCHEDULES:
-        O.axpy_f32(3.0, x, y)
-        O.stencil2d5(grid)
-        nbytes += 12 * x.size + 8 * grid.size
-    return nbytes
-
-
-def cpu_baseline(budget_s=10.0):
-    from paper_2106_03219_gb300 import inputs
-    n, g = 1 << 22, 1024
-    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
-    grid = inputs.grid_f32(g, g, 0)
-    oracle_sample_step(x, y, grid)  # builds / loads the oracle
     t0 = time.perf_counter()
-    nbytes, steps = 0, 0
-    while time.perf_counter() - t0 < budget_s:
-        nbytes += oracle_sample_step(x, y, grid)
-        steps += 1
-    dt = time.perf_counter() - t0
-    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d oracle steps of fp32 axpy n=2^22 + 2D stencil %dx%d x 6 schedules "
-                      "(single-threaded C), %.1f s" % (steps, g, g, dt)}
+    for _ in SCHEDULES:
+        y[...] = O.axpy_f32(3.0, x, y)
+        O.stencil2d5(grid)
+    return time.perf_counter() - t0, (12 * x.size + 8 * grid.size) * len(SCHEDULES)
+
+
+class CpuStep:
+    """The worksharing step on all host cores: every schedule's axpy and
+    stencil split into one contiguous slice (rows for the stencil) per core."""
+
+    def __init__(self, pool, x, y, grid):
+        self.pool = pool
+        self.sx, _ = pool.share(x)
+        self.sy, _ = pool.share(y)
+        self.sg, _ = pool.share(grid)
+        self.so, _ = pool.share(np.zeros_like(grid))
+        self.n, self.ny = x.size, grid.shape[0]
+        self.nbytes = (12 * x.size + 8 * grid.size) * len(SCHEDULES)
+
+    def run(self):
+        t = 0.0
+        for _ in SCHEDULES:
+            t += self.pool.run("axpy_f32", [self.sx, self.sy], self.n, extra=3.0)[0]
+            t += self.pool.run("stencil2d", [self.sg, self.so], self.ny)[0]
+        return t
+
+
+def worksharing_inputs():
+    from paper_2106_03219_gb300 import inputs
+    return (inputs.f32_uniform01(N_AXPY, 0), inputs.f32_uniform01(N_AXPY, 1),
+            inputs.grid_f32(GRID, GRID, 0))
+
+
+def cpu_worksharing(pool, steps=3):
+    """cpu_baseline of the main line: the full worksharing step (axpy 2^26 and
+    the 4096^2 stencil, x 6 schedules) on all cores, best of `steps`, and on
+    one core (one step)."""
+    x, y, grid = worksharing_inputs()
+    st = CpuStep(pool, x, y, grid)
+    t_all = min(st.run() for _ in range(steps))
+    t_one, nbytes = oracle_step_one_core(x, y.copy(), grid)
+    return {"value": nbytes / t_all / 1e9, "unit": UNIT, "cores": pool.n, "kind": "oracle",
+            "sample": "the full step (fp32 axpy n=2^26 + 2D stencil 4096x4096, x 6 schedules), "
+                      "best of %d, oracle on %d cores (one slice per core)" % (steps, pool.n),
+            "one_core": {"value": nbytes / t_one / 1e9, "unit": UNIT, "cores": 1,
+                         "sample": "one full step, single-threaded oracle"}}
+
+
+def cpu_single_region(pool):
+    """Configuration 1 on the CPU: int32 axpy y = 3x + y over n = 2^20 and the
+    int64 sum of the new y; median of 5 on one core, and on all cores."""
+    import oracle as O
+    from paper_2106_03219_gb300 import inputs
+    n = 1 << 20
+    x, y = inputs.int32_uniform(n, 0), inputs.int32_uniform(n, 1)
+    ts = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        yn = O.axpy_i32(3, x, y)
+        O.sum_int(yn)
+        ts.append(time.perf_counter() - t0)
+    sx, _ = pool.share(x)
+    ta = []
+    for _ in range(5):
+        sy, _ = pool.share(y)
+        ta.append(pool.run("axpy_i32_sum", [sx, sy], n, extra=3)[0])
+    t1, tall = statistics.median(ts), statistics.median(ta)
+    return {"one_core_ms": t1 * 1e3, "one_core_GBps": 12 * n / t1 / 1e9,
+            "all_cores_ms": tall * 1e3, "all_cores_GBps": 12 * n / tall / 1e9, "cores": pool.n}
+
+
+def cpu_reductions(pool, arrays, gpu):
+    """Exact sums of the reduction inputs on all cores (the oracle's exact
+    expansions per slice, combined exactly), the error of every GPU variant
+    against them, and the CPU baselines of the reduction: the exact oracle
+    and the plain fp64 loop, on all cores and on one core (a 2^24 sample)."""
+    import oracle as O
+    out = {}
+    for name, a in arrays.items():
+        bf = name == "bf16_sum"
+        if name == "int64_sum":
+            want = O.sum_int(a)
+            out[name] = {"exact": want, "gpu": gpu[name]["shipped"],
+                         "bit_exact": gpu[name]["shipped"] == want}
+            continue
+        spec, _ = pool.share(a)
+        t_exact, terms = pool.run("exact_terms", [spec], a.size, extra=1 if bf else 0)
+        exact = O.exact_sum_f64(np.concatenate([np.asarray(t) for t in terms]))
+        vals = (a.astype(np.uint32) << 16).view(np.float32) if bf else a
+        sabs = O.exact_abs_sum_f32(vals[: 1 << 24]) * (a.size / min(a.size, 1 << 24))
+        row = {"exact": exact, "abs_sum_estimate": sabs}
+        for var in ("shipped", "comp_f32", "naive_f32"):
+            v = gpu[name][var]
+            err = abs(v - exact)
+            row[var] = {"value": v, "rel_err": err / abs(exact) if exact else None,
+                        "err_over_abs_sum": err / sabs if sabs else None,
+                        "within_1e-6": err <= 1e-6 * max(abs(exact), 2.0 ** -24 * sabs)}
+        if name == "fp32_pm1_sum":
+            for op in ("max", "min"):
+                got = gpu["fp32_" + op]["value"]
+                gpu["fp32_" + op]["vs_oracle"] = {"oracle": O.max_min(a, op),
+                                                  "bit_exact": got == O.max_min(a, op)}
+            # CPU baselines of the reduction on this array (1 GiB of fp32)
+            t_plain = pool.run("plain_sum", [spec], a.size)[0]
+            s = a[: 1 << 24]
+            t0 = time.perf_counter()
+            O.exact_sum_f32(s)
+            t1 = time.perf_counter()
+            O.plain_sum_f32(s)
+            t2 = time.perf_counter()
+            row["cpu_baseline"] = {
+                "exact_all_cores_GBps": a.nbytes / t_exact / 1e9,
+                "plain_fp64_all_cores_GBps": a.nbytes / t_plain / 1e9,
+                "exact_one_core_GBps": s.nbytes / (t1 - t0) / 1e9,
+                "plain_fp64_one_core_GBps": s.nbytes / (t2 - t1) / 1e9,
+                "cores": pool.n,
+                "sample": "all cores: the whole n=2^28 array; one core: its first 2^24 elements"}
+        out[name] = row
+    return out
+
+
+def cpu_batched(pool):
+    """The 4096-region batch on the CPU: the oracle's per-region loop (axpy,
+    exact dot, 1-D stencil), regions dealt round robin to the cores; and on
+    one core."""
+    import oracle as O
+    from paper_2106_03219_gb300 import inputs
+    n, kind, off = inputs.batched_regions()
+    total = int(off[-1] + (n[-1] + 63) // 64 * 64)
+    x, y = inputs.f32_uniform01(total, 0), inputs.f32_uniform01(total, 1)
+    table = np.stack([kind.astype(np.int64), off.astype(np.int64), n.astype(np.int64)], 1)
+    # deal regions so every core gets a similar number of iterations
+    order = np.argsort(-n)
+    owner = np.zeros(len(n), np.int64)
+    load = np.zeros(pool.n)
+    for r in order:
+        k = int(np.argmin(load))
+        owner[r] = k
+        load[k] += n[r]
+    perm = np.argsort(owner, kind="stable")
+    tab = table[perm]
+    cnt = np.bincount(owner, minlength=pool.n)
+    cuts = np.r_[0, np.cumsum(cnt)]
+    sx, _ = pool.share(x)
+    sy, _ = pool.share(y)
+    so, _ = pool.share(np.zeros(total, np.float32))
+    st, _ = pool.share(tab)
+    t_all = pool.run("regions", [sx, sy, so, st], len(n),
+                     parts=list(zip(cuts[:-1].tolist(), cuts[1:].tolist())))[0]
+    yy = y.copy()
+    t0 = time.perf_counter()
+    for k, o, m in table:
+        if k == inputs.KIND_AXPY:
+            yy[o:o + m] = O.axpy_f32(3.0, x[o:o + m], yy[o:o + m])
+        elif k == inputs.KIND_DOT:
+            O.exact_dot_f32(x[o:o + m], yy[o:o + m])
+        else:
+            O.stencil1d3(x[o:o + m])
+    t_one = time.perf_counter() - t0
+    from paper_2106_03219_gb300.batched import BYTES_PER_ITER
+    nbytes = int(sum(BYTES_PER_ITER[int(k)] * int(m) for k, m in zip(kind, n)))
+    return {"all_cores_regions_per_s": len(n) / t_all, "all_cores_GBps": nbytes / t_all / 1e9,
+            "one_core_regions_per_s": len(n) / t_one, "one_core_GBps": nbytes / t_one / 1e9,
+            "cores": pool.n}
+
+
+def cpu_mlp(reps=20):
+    """One FP64 training step of the cost model on the oracle (forward,
+    loss, backward, Adam) on a batch of 256, one core.  A step is about 3
+    MFLOP, too small to split across processes."""
+    import oracle as O
+    rng = np.random.default_rng(0)
+    p = rng.normal(0, 0.1, O.mlp_nparam())
+    X, Y = rng.normal(size=(256, 16)), rng.normal(size=(256, 12))
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    ts = []
+    for t in range(1, reps + 1):
+        t0 = time.perf_counter()
+        _, g = O.mlp_loss_grad(p, X, Y)
+        O.adam_step(p, g, m, v, t)
+        ts.append(time.perf_counter() - t0)
+    return {"one_core_ms_per_step": statistics.median(ts) * 1e3, "batch": 256, "cores": 1}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle on the host cores, on this bench's
+    workload (the full worksharing step), with the same metric and unit."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from paper_2106_03219_gb300 import inputs
-    n, g = 1 << 22, 1024
-    x, y = inputs.f32_uniform01(n, 0), inputs.f32_uniform01(n, 1)
-    grid = inputs.grid_f32(g, g, 0)
-    for _ in range(args.warmup):
-        oracle_sample_step(x, y, grid)
-    t0 = time.perf_counter()
-    nbytes = 0
-    for _ in range(args.steps):
-        nbytes += oracle_sample_step(x, y, grid)
-    dt = time.perf_counter() - t0
-    v = nbytes / dt / 1e9
-    sample = ("per step: fp32 axpy n=2^22 + 2D stencil %dx%d x 6 schedules on the CPU oracle "
-              "(single-threaded C)" % (g, g))
+    from oracle import cores
+    pool = cores.Cores()
+    try:
+        x, y, grid = worksharing_inputs()
+        st = CpuStep(pool, x, y, grid)
+        for _ in range(args.warmup):
+            st.run()
+        t = sum(st.run() for _ in range(args.steps))
+        v = st.nbytes * args.steps / t / 1e9
+        t_one, nbytes = oracle_step_one_core(x, y.copy(), grid)
+    finally:
+        pool.close()
+    sample = ("per step: the full workload (fp32 axpy n=2^26 + 2D stencil 4096x4096, x 6 "
+              "schedules), oracle on %d cores (one slice per core)" % pool.n)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_dict(None),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.n, "kind": "oracle",
+                             "sample": sample,
+                             "one_core": {"value": nbytes / t_one / 1e9, "unit": UNIT,
+                                          "cores": 1, "sample": "one full step"}},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -354,13 +527,32 @@ def main():
     e2e_line = {"value": step_bytes * ws / (e2e_val * 1e-3) / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
 
-    reductions = measure_reductions(rt, R, torch, inputs) if not args.no_extras else None
+    # every kernel alone, back to back on rotating buffers (steady state)
+    steady = measure_kernels_steady(rt, R, torch, launches, plan, peak) \
+        if not args.no_extras else None
+    single = measure_single_region(rt, R, torch, inputs) if not args.no_extras else None
+    sharded_red = measure_sharded(rt, R, torch, inputs, ws, rank) if not args.no_extras else None
+    red_gpu, red_arrays = measure_reductions(rt, R, torch, inputs) \
+        if not args.no_extras else (None, None)
     batched_forms = measure_batched(rt) if not args.no_extras else None
     learned_eval = measure_learned(rt) if not args.no_extras else None
 
-    cpu = None
+    cpu, cpu_legs = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        from oracle import cores
+        pool = cores.Cores()
+        try:
+            cpu = cpu_worksharing(pool)
+            if not args.no_extras:
+                cpu_legs = {"single_region": cpu_single_region(pool),
+                            "batched": cpu_batched(pool), "mlp_step": cpu_mlp()}
+                red_check = cpu_reductions(pool, red_arrays, red_gpu)
+                for k, v in red_check.items():
+                    red_gpu[k]["vs_oracle"] = v
+        finally:
+            pool.close()
+    reductions = red_gpu
+    del red_arrays
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -368,9 +560,10 @@ def main():
                 "dtype": "f32", "data": "synthetic", "config": config_dict(points),
                 "e2e": e2e_line, "roofline": roofline, "cpu_baseline": cpu,
                 "gpu_launches": len(plan) * args.steps, "clocks": clk,
-                "kernels": kernels, "reductions": reductions, "batched": batched_forms,
-                "learned": learned_eval,
-                "source_hash": source_hash()}
+                "kernels": kernels, "kernels_steady": steady, "single_region": single,
+                "sharded_reduction": sharded_red,
+                "reductions": reductions, "batched": batched_forms, "learned": learned_eval,
+                "cpu_legs": cpu_legs, "source_hash": source_hash()}
         print(json.dumps(line))
     rt.close()
     if ws > 1:
@@ -451,20 +644,24 @@ def run_single(rt, torch, plan, args):
 
 def measure_reductions(rt, R, torch, inputs, n=1 << 28, reps=5):
     """GB/s of the reduction configuration: n = 2^28 sums (fp32 uniform and
-    lognormal, bf16, int64) and fp32 max / min, shipped precision, 4 teams
-    per SM x 512 threads; inputs (0.5-2 GB) are larger than L2."""
-    import numpy as np
-    out = {}
+    lognormal, bf16, int64) and fp32 max / min at the shipped precision
+    (compensated fp32, fp64 combine), 4 teams per SM x 512 threads; inputs
+    (0.5-2 GB) are larger than L2.  The fp sums are also run at the two
+    comparison precisions (compensated fp32 with an fp32 combine, plain fp32)
+    for the error report.  Returns (per-result dict, host arrays)."""
+    out, arrays = {}, {}
     sms = rt.sm_count
     res = torch.zeros(1, dtype=torch.float64, device="cuda")
     resi = torch.zeros(1, dtype=torch.int64, device="cuda")
     peak, _ = measured_peaks()
     cases = [("fp32_pm1_sum", lambda: inputs.f32_uniform_pm1(n, 0), R.OP_SUM, res),
              ("fp32_lognormal_sum", lambda: inputs.f32_lognormal_signed(n, 0), R.OP_SUM, res),
-             ("bf16_sum", lambda: inputs.bf16_uniform_pm1(n, 0).view(np.int16), R.OP_SUM, res),
+             ("bf16_sum", lambda: inputs.bf16_uniform_pm1(n, 0), R.OP_SUM, res),
              ("int64_sum", lambda: inputs.int64_uniform(n, 0), R.OP_SUM, resi)]
     for name, gen, op, r in cases:
-        t = torch.from_numpy(gen()).cuda()
+        a = gen()
+        arrays[name] = a
+        t = torch.from_numpy(a.view(np.int16) if name == "bf16_sum" else a).cuda()
         if name == "bf16_sum":
             t = t.view(torch.bfloat16)
         ops = [(name, op)] if name != "fp32_pm1_sum" else [(name, op), ("fp32_max", R.OP_MAX),
@@ -480,9 +677,136 @@ def measure_reductions(rt, R, torch, inputs, n=1 << 28, reps=5):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             gbs = t.numel() * t.element_size() / (ms * 1e-3) / 1e9
-            out[label] = {"ms": ms, "GBps": gbs, "frac": gbs / peak}
+            v = r.cpu()[0].item()
+            if label in ("fp32_max", "fp32_min"):
+                out[label] = {"ms": ms, "GBps": gbs, "frac": gbs / peak, "value": v}
+                continue
+            out[label] = {"ms": ms, "GBps": gbs, "frac": gbs / peak, "shipped": v}
+            if o == R.OP_SUM and name != "int64_sum":
+                for var, prec in (("comp_f32", R.PREC_COMP_F32), ("naive_f32", R.PREC_NAIVE_F32)):
+                    rt.reduce(o, t, r, prec, 4 * sms, 512)
+                    out[label][var] = r.cpu()[0].item()
         del t
     assert rt.sync_status() == 0
+    return out, arrays
+
+
+def measure_sharded(rt, R, torch, inputs, ws, rank, n=1 << 28, reps=5):
+    """The reduction configuration's fp32 sum (n = 2^28, U[-1,1]) sharded over
+    the ranks (strong scaling): rank r reduces its contiguous block on its own
+    GPU, then one all-gather of 8 bytes per rank and the rank-order fp64
+    combine.  Time: the slowest rank's local reduction (events, mean of
+    `reps`) plus the exchange (host clock, barrier-to-barrier)."""
+    from paper_2106_03219_gb300 import sharded
+    s, c = sharded.rank_block(n, ws, rank)
+    a = inputs.f32_uniform_pm1(n, 0)
+    shard = torch.from_numpy(a[s:s + c]).cuda()
+    del a
+    sms = rt.sm_count
+    stream = torch.cuda.current_stream()
+    sharded.reduce_shard(rt, R.OP_SUM, shard, R.PREC_COMP_F64, 4 * sms, 512)
+    torch.cuda.synchronize()
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        rt.reduce(R.OP_SUM, shard, res, R.PREC_COMP_F64, 4 * sms, 512, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_local = max_over_ranks(e0.elapsed_time(e1) / reps, ws)
+    v = res.item()
+    barrier(ws)
+    t0 = time.perf_counter()
+    total = sharded.combine(sharded.gather_partials(v, False), R.OP_SUM, False)
+    barrier(ws)
+    ms_x = max_over_ranks((time.perf_counter() - t0) * 1e3, ws)
+    assert rt.sync_status() == 0
+    return {"n": n, "ranks": ws, "block": [s, c], "local_ms": ms_local, "exchange_ms": ms_x,
+            "GBps": 4 * n / ((ms_local + ms_x) * 1e-3) / 1e9, "result": total,
+            "scaling": "strong"}
+
+
+def measure_single_region(rt, R, torch, inputs, reps=200):
+    """Configuration 1: int32 axpy y = 3x + y over n = 2^20 with an int64 sum
+    reduction, 4 teams x 128 threads, schedule(static).  Its 12.6 MB stay in
+    L2 between back-to-back launches, so it is reported as time, GB/s and
+    launch latency, not against the HBM roofline."""
+    n = 1 << 20
+    x = torch.from_numpy(inputs.int32_uniform(n, 0)).cuda()
+    y = torch.from_numpy(inputs.int32_uniform(n, 1)).cuda()
+    r = torch.zeros(1, dtype=torch.int64, device="cuda")
+    desc = R.loop_desc(R.BODY_AXPY, n=n, x=x, y=y, alpha=3)
+    red = R.ReduceDesc(R.OP_SUM, 0, r.data_ptr())
+    stream = torch.cuda.current_stream()
+    go = lambda: rt.launch_region(desc, R.SCHED_STATIC, 0, 4, 128, red=red, stream=stream)
+    for _ in range(5):
+        go()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        go()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    # host cost of one call (argument checks + launch), no synchronisation
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        go()
+    t_call = (time.perf_counter() - t0) / reps
+    torch.cuda.synchronize()
+    # one launch from the host call to its completion seen by the host
+    lat = []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        go()
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - t0)
+    assert rt.sync_status() == 0
+    # the same launch on a fresh box stays 4 teams: G = 4 uses 4 of the SMs
+    return {"n": n, "teams": 4, "threads": 128, "device_ms_per_launch": ms,
+            "GBps": 12 * n / (ms * 1e-3) / 1e9, "host_call_us": t_call * 1e6,
+            "launch_to_done_us": statistics.median(lat) * 1e6, "l2_resident": True}
+
+
+def measure_kernels_steady(rt, R, torch, launches, plan, peak, nsets=4, reps=3):
+    """Every kernel of the step alone, launched back to back over `nsets`
+    copies of its buffers in turn (each launch's inputs were last touched
+    three launches earlier, more than L2 ago), so each launch pays the
+    write-back of the previous one's output as it would in a stream of its
+    own kind.  In the step itself a stencil launch follows an 805 MB axpy and
+    pays for the write-back of that axpy's dirty lines (up to L2's size),
+    and the axpy after it pays less; these figures take that cross-charge
+    out."""
+    from paper_2106_03219_gb300 import inputs
+    sets = []
+    for k in range(nsets):
+        xx = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 0)).cuda()
+        yy = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 1)).cuda()
+        gg = torch.from_numpy(inputs.grid_f32(GRID, GRID, 0)).cuda()
+        oo = torch.empty_like(gg)
+        sets.append(((xx, yy, gg, oo), launches(xx, yy, gg, oo)))
+    stream = torch.cuda.current_stream()
+    out = {}
+    for i, (name, nbytes, *_r) in enumerate(plan):
+        for _, L in sets:
+            _, _, d, sched, chunk, G, T = L[i]
+            rt.launch_region(d, sched, chunk, G, T, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            for _, L in sets:
+                _, _, d, sched, chunk, G, T = L[i]
+                rt.launch_region(d, sched, chunk, G, T, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (reps * nsets)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "GBps": gbs, "frac": gbs / peak}
+    assert rt.sync_status() == 0
+    del sets
     return out
 
 
@@ -500,17 +824,19 @@ def measure_batched(rt):
 
 def measure_learned(rt, count=2000, seed=1):
     """The committed cost model against the plain heuristic on held-out loops
-    (seed 1, never used in training): measured total time of each one's picks
-    and of the per-loop best of the 12 configurations."""
-    import numpy as np
+    (seed 1, never used in training): each loop's two picks timed
+    interleaved (5 launches each, medians), the whole set three times in
+    fresh orders (gain mean and spread); and, from one timing of all 12
+    configurations, the gap of each pick to the per-loop best."""
     from paper_2106_03219_gb300 import learned
     model = learned.Model.load()
     if model is None:
         return None
     buf = learned.LoopBuffers()
     kind, n = learned.make_loops(count, seed)
+    rep = learned.compare_picks(rt, model, kind, n, buf, reps=5, rounds=3)
     T = learned.time_loops(rt, kind, n, buf, reps=3)
-    rep = learned.evaluate(rt, model, kind, n, T, buf)
+    rep["vs_best"] = learned.evaluate(rt, model, kind, n, T, buf)
     del buf
     return rep
 

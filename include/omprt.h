@@ -217,22 +217,23 @@ omprt_status omprt_alloc_shared(omprt_ctx *ctx, size_t bytes_per_team);
 omprt_status omprt_set_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_team);
 
 /* Shared memory per CTA that the 2-D stencil (fp32, no reduction) may use
- * under static, static(c) and dynamic(c) to stage its input.  Each team's
- * block of the collapsed loop, plus one grid row on each side, is copied into
- * shared memory by one bulk copy (the team-shared state of Sec. 3.1, "Global
- * Shared Variables"), and every thread then runs exactly the iterations the
- * schedule gives it (Sec. 1, Sec. 2 worksharing), reading its operands there.
- * Dynamic chunks are claimed from the team's counter in shared memory, 32 per
- * warp, lane l running chunk base + l; a thread's claims increase.  A launch
- * has at most as many CTAs as fit the device at once; CTA k plays the
- * consecutive teams [k G / P, (k + 1) G / P) in turn, in passes of whole teams
- * whose two windows alternate (the next pass's copy in flight while one
- * computes).  The form applies when nx is a multiple of 4, n < 2^32, both
- * pointers are 16-byte aligned and two windows of one team (its block plus
- * two rows) fit `bytes` and the device's per-block shared memory; other
- * launches run the forms of omprt_set_stage_bytes.  bytes is rounded down to
- * 16; 0 turns this form off; more than the device's per-block shared memory is
- * OMPRT_ERR_INVALID.  Default after init: 192 KiB. */
+ * under dynamic(c) and static(1) to stream its input.  A launch has at most as
+ * many CTAs as fit the device at once; CTA k plays the consecutive teams
+ * [k G / P, (k + 1) G / P) (OpenMP does not make teams run at the same time)
+ * and reads their range of the grid, plus one row on each side, once, through
+ * a ring of row-sized segments in shared memory filled by bulk copies (the
+ * team-shared state of Sec. 3.1, "Global Shared Variables"): a producer warp
+ * refills a slot as soon as every team group has released it.  The CTA's
+ * threads form groups of thread_limit, each playing one team at a time; every
+ * thread runs exactly the iterations the schedule gives it (Sec. 1, Sec. 2
+ * worksharing), reading its operands from the ring.  Dynamic chunks are
+ * claimed from the team's counter in shared memory, 32 per warp, lane l
+ * running chunk base + l; a thread's claims increase.  The form applies when
+ * nx is a multiple of 4, n < 2^32, both pointers are 16-byte aligned,
+ * thread_limit <= 512 and the ring holds one team's rows with room to spare;
+ * other launches run the forms of omprt_set_stage_bytes.  bytes is rounded
+ * down to 16; 0 turns this form off; more than the device's per-block shared
+ * memory is OMPRT_ERR_INVALID.  Default after init: 226 KiB. */
 omprt_status omprt_set_stencil_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_cta);
 
 /*

@@ -5,9 +5,11 @@ teams x threads and records the fastest point; the table is what the
 benchmark and the batched executor use.  The team counts include powers of
 two besides multiples of the SM count: with n a power of two they make every
 team's block start on a 32-byte boundary, so per-thread chunks are whole
-vectors.  Timing: CUDA events on the launching
-stream, median of `reps` launches, with an L2 flush (a write of a buffer
-larger than L2) before every timed launch.
+vectors.  Timing: CUDA events on the launching stream around launches that
+go back to back over four copies of the buffers in turn (each launch's
+inputs were last touched three launches earlier, more than L2 ago, and each
+launch pays the write-back of the previous one's output, as in a stream of
+such launches); the mean of `reps` rounds.
 """
 import json
 import os
@@ -16,7 +18,7 @@ import statistics
 PKG = os.path.dirname(os.path.abspath(__file__))
 SWEEP_TABLE = os.path.join(PKG, "tuned", "sweep_gb300.json")
 
-TEAMS = (148, 296, 592, 1024, 1184, 2048, 2368, 4096, 8192)
+TEAMS = (148, 296, 592, 1024, 1184, 2048, 2368, 4096, 8192, 16384)
 THREADS = (32, 64, 128, 256, 512, 1024)
 SCHEDULES = [("static1", 1, 1), ("static8", 1, 8), ("static64", 1, 64), ("static", 0, 0),
              ("dynamic256", 2, 256), ("auto", 3, 0)]
@@ -74,55 +76,42 @@ def load_sweep_table(path=SWEEP_TABLE):
     return json.load(open(path)).get("best")
 
 
-class Timer:
-    """Median device time of a launch callable, L2 flushed before each launch."""
-
-    def __init__(self, torch, l2_bytes, reps=5):
-        self.torch = torch
-        self.reps = reps
-        self.flush = torch.empty(max(2 * l2_bytes, 1 << 28) // 4, dtype=torch.float32,
-                                 device="cuda")
-        self.e0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
-        self.e1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
-
-    def __call__(self, fn):
-        torch = self.torch
-        s = torch.cuda.current_stream()
-        fn()  # warm
-        for k in range(self.reps):
-            self.flush.zero_()
-            self.e0[k].record(s)
-            fn()
-            self.e1[k].record(s)
-        torch.cuda.synchronize()
-        return statistics.median(self.e0[k].elapsed_time(self.e1[k]) for k in range(self.reps))
-
-
-def sweep(rt, n_axpy=1 << 26, grid=4096, reps=5, teams=TEAMS, threads=THREADS, log=None):
+def sweep(rt, n_axpy=1 << 26, grid=4096, reps=3, teams=TEAMS, threads=THREADS, log=None,
+          nsets=4):
     """The worksharing sweep: axpy (12 B/iter) and 2-D stencil (8 B/point)
     under every schedule at every (teams, threads).  Returns (rows, best)."""
     import torch
     from . import inputs
     from . import omprt as R
 
-    l2 = torch.cuda.get_device_properties(0).L2_cache_size
-    timer = Timer(torch, l2, reps)
-    x = torch.from_numpy(inputs.f32_uniform01(n_axpy, 0)).cuda()
-    y = torch.from_numpy(inputs.f32_uniform01(n_axpy, 1)).cuda()
-    g = torch.from_numpy(inputs.grid_f32(grid, grid, 0)).cuda()
-    o = torch.empty_like(g)
-    bodies = {
-        "axpy": (R.loop_desc(R.BODY_AXPY, n=n_axpy, x=x, y=y, alpha=3.0), 12 * n_axpy),
-        "stencil2d": (R.loop_desc(R.BODY_STENCIL2D5, n=grid * grid, x=g, out=o, nx=grid,
-                                  ny=grid), 8 * grid * grid),
-    }
+    sets = []
+    for _ in range(nsets):
+        x = torch.from_numpy(inputs.f32_uniform01(n_axpy, 0)).cuda()
+        y = torch.from_numpy(inputs.f32_uniform01(n_axpy, 1)).cuda()
+        g = torch.from_numpy(inputs.grid_f32(grid, grid, 0)).cuda()
+        o = torch.empty_like(g)
+        sets.append({
+            "axpy": R.loop_desc(R.BODY_AXPY, n=n_axpy, x=x, y=y, alpha=3.0),
+            "stencil2d": R.loop_desc(R.BODY_STENCIL2D5, n=grid * grid, x=g, out=o, nx=grid,
+                                     ny=grid)})
+    nbytes = {"axpy": 12 * n_axpy, "stencil2d": 8 * grid * grid}
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rows, best = [], {}
-    for bname, (desc, nbytes) in bodies.items():
+    for bname in ("axpy", "stencil2d"):
         for label, sched, chunk in SCHEDULES:
             for G in teams:
                 for T in threads:
-                    ms = timer(lambda: rt.launch_region(desc, sched, chunk, G, T))
-                    gbs = nbytes / (ms * 1e-3) / 1e9
+                    for st in sets:
+                        rt.launch_region(st[bname], sched, chunk, G, T, stream=stream)
+                    e0.record(stream)
+                    for _ in range(reps):
+                        for st in sets:
+                            rt.launch_region(st[bname], sched, chunk, G, T, stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / (reps * nsets)
+                    gbs = nbytes[bname] / (ms * 1e-3) / 1e9
                     rows.append({"body": bname, "schedule": label, "teams": G, "threads": T,
                                  "ms": ms, "GBps": gbs})
                     key = "%s/%s" % (bname, label)
@@ -142,7 +131,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=SWEEP_TABLE)
     ap.add_argument("--rows", default=None, help="also write every measured point here")
-    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch", default=None, help="tune the batched executor, write here")
     args = ap.parse_args()
     torch.cuda.init()

@@ -18,7 +18,7 @@ constexpr size_t kDynBytes = 8ull * OMPRT_MAX_RED_TEAMS;
 constexpr size_t kSlotBytes = kTicketBytes + kPartialBytes + kDynBytes;
 constexpr uint32_t kMaxStackBytes = 200u * 1024u;
 // shared memory per CTA for the staged 2-D stencil windows (two windows)
-constexpr uint32_t kStencilStageDefault = 192u * 1024u;
+constexpr uint32_t kStencilStageDefault = 226u * 1024u;
 
 bool is_int_type(int32_t t) { return t >= OMPRT_I32 && t <= OMPRT_U64; }
 
@@ -441,8 +441,14 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
     if (e != cudaErrorNotSupported) return from_cuda(e);
     cudaGetLastError();
   }
+  // the staged ring form of the 2-D stencil where it beats the others
+  // (measured at 4096^2, best teams x threads of each form): dynamic(256)
+  // 0.44 of the copy rate against 0.25 plain, static(1) 0.42 against 0.40;
+  // static and static(c > 1) stay with their own forms (static 0.59 plain
+  // against 0.51 staged, static(8) 0.53 against 0.52, static(64) 0.45 in the
+  // row ring against 0.44)
   if (d->body == OMPRT_BODY_STENCIL2D5 && acc == kAccNone && d->data_type == OMPRT_F32 &&
-      (ksched == kStatic || ksched == kChunked || ksched == kDynamic) &&
+      (ksched == kDynamic || (ksched == kChunked && chunk == 1)) &&
       c->stencil_stage_bytes != 0) {
     e = launch_stencil2d_owner(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny, ksched,
                                (uint64_t)chunk, (float)d->c0, (float)d->c1, (unsigned)teams,

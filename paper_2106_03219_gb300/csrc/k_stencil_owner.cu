@@ -47,7 +47,7 @@
 
 namespace rt {
 
-constexpr uint32_t kOwnerMaxPassTeams = 64;
+constexpr uint32_t kOwnerMaxGroups = 15;  // named barriers 1 .. 15, one per group
 constexpr uint32_t kOwnerMaxSlots = 64;
 constexpr uint64_t kOwnerWaitNs = 1000000000ull;  // 1 s: a pass takes microseconds
 
@@ -62,7 +62,7 @@ struct OwnerArgs {
   uint32_t chunk;         // static(c) / dynamic(c): c (at most q + 1); static: 0
   uint32_t seg;           // L: floats per ring segment (a multiple of 32)
   uint32_t slots;         // S: segments the ring holds, 2 .. kOwnerMaxSlots
-  uint32_t pass_teams;    // teams per pass, 1 .. kOwnerMaxPassTeams
+  uint32_t pass_teams;    // unused (1)
   uint64_t nx_magic;      // ceil(2^64 / nx): the row of i < 2^32 is umulhi(i, magic)
   float c0, c1;
   uint32_t* status;
@@ -247,18 +247,19 @@ __device__ __forceinline__ void owner_piece(const OwnerArgs& A, const Win& W, ui
 
 template <int SCHED>
 __global__ void __launch_bounds__(1024) stencil2d_owner_kernel(const OwnerArgs A) {
-  __shared__ __align__(8) uint64_t bars[kOwnerMaxSlots];
-  __shared__ uint32_t ctr[2][kOwnerMaxPassTeams];  // dynamic: per-team claim counters
+  __shared__ __align__(8) uint64_t full[kOwnerMaxSlots], empty[kOwnerMaxSlots];
+  __shared__ uint32_t ctr[kOwnerMaxGroups][2];  // dynamic: each group's claim counters
   __shared__ int s_bad;
-  float* const ring = (float*)(((uintptr_t)rt_dyn_smem + 127) & ~(uintptr_t)127);
+  // the ring on a 128-byte boundary, addressed from the shared array itself so
+  // that every access compiles to a shared-memory load
+  float* const ring = (float*)(rt_dyn_smem + ((128u - (smem_addr(rt_dyn_smem) & 127u)) & 127u));
   const uint32_t t = threadIdx.x, lane = t & 31u;
   const uint32_t Tl = A.T, K = A.groups, gr = t / Tl, tt = t - gr * Tl;
   const uint32_t P = gridDim.x, k = blockIdx.x;
   const uint32_t g0 = (uint32_t)((uint64_t)k * A.G / P);
   const uint32_t g1 = (uint32_t)((uint64_t)(k + 1) * A.G / P);
   if (g0 >= g1) return;  // uniform; never with P <= G
-  const uint32_t PT = A.pass_teams, L = A.seg, S = A.slots;
-  const uint32_t npass = (g1 - g0 + PT - 1) / PT;
+  const uint32_t L = A.seg, S = A.slots;
   // this CTA's input stream: its teams' range plus one row on each side, in
   // whole 16-byte units
   uint32_t E0, E1, tmp;
@@ -267,54 +268,92 @@ __global__ void __launch_bounds__(1024) stencil2d_owner_kernel(const OwnerArgs A
   const uint32_t base = (E0 > A.nx ? E0 - A.nx : 0u) & ~3u;
   const uint32_t send = ((E1 < A.n - A.nx ? E1 + A.nx : A.n) + 3u) & ~3u;  // n % 4 == 0
   const uint32_t nseg = (send - base + L - 1) / L;
-  const uint32_t bar0 = smem_addr(&bars[0]);
+  const uint32_t full0 = smem_addr(&full[0]), empty0 = smem_addr(&empty[0]);
   if (t == 0) {
-    for (uint32_t i = 0; i < S; ++i) mbar_init(bar0 + 8 * i);
+    for (uint32_t i = 0; i < S; ++i) {
+      mbar_init(full0 + 8 * i);               // one arrival (with the bytes) per fill
+      mbar_init_count(empty0 + 8 * i, K);     // one arrival per group per release
+    }
     s_bad = 0;
   }
-  if (SCHED == kDynamic && t < kOwnerMaxPassTeams) ctr[0][t] = 0;
+  if (SCHED == kDynamic && t < 2 * kOwnerMaxGroups) ctr[t >> 1][t & 1] = 0;
   __syncthreads();
-  // segment i: stream elements [base + i L, min(base + (i + 1) L, send)) into slot i mod S
-  auto issue = [&](uint32_t i) {
-    const uint32_t lo = base + i * L;
-    const uint32_t len = send - lo < L ? send - lo : L;
-    const uint32_t b = bar0 + 8 * (i % S);
-    mbar_expect_tx(b, len * 4u);
-    bulk_g2s(ring + (size_t)(i % S) * L, A.in + lo, len * 4u, b);
+  // the first / one past the last segment team g's points and neighbours lie in
+  auto seg_lo = [&](uint32_t g) {
+    uint32_t bs, bn;
+    owner_block(A, g, bs, bn);
+    return (((bs > A.nx ? bs - A.nx : 0u) & ~3u) - base) / L;
   };
-  // the first segment pass qp needs: its points' north neighbours and its
-  // first point's west neighbour
-  auto first_seg = [&](uint32_t qp) {
-    uint32_t Sq;
-    owner_block(A, g0 + qp * PT, Sq, tmp);
-    const uint32_t need = (Sq > A.nx ? Sq - A.nx : 0u) & ~3u;
-    return (need - base) / L;
+  auto seg_hi = [&](uint32_t g) {
+    uint32_t bs, bn;
+    owner_block(A, g, bs, bn);
+    const uint32_t e = bs + bn < A.n - A.nx ? bs + bn + A.nx : A.n;
+    return (e - base + L - 1) / L;
   };
-  uint32_t next = 0;  // thread 0: the next segment to issue
-  if (t == 0)
-    for (; next < nseg && next < S; ++next) issue(next);
-  uint32_t waited = 0;  // every thread: segments [0, waited) seen complete
-  const Win W{ring, base, S * L};
-  for (uint32_t qp = 0; qp < npass; ++qp) {
-    const uint32_t ga = g0 + qp * PT, gb = ga + PT < g1 ? ga + PT : g1;
-    uint32_t Eq;
-    owner_block(A, gb, Eq, tmp);
-    // the last segment the pass needs: its points' south neighbours and its
-    // last point's east neighbour
-    const uint32_t need_end = Eq < A.n - A.nx ? Eq + A.nx : A.n;
-    const uint32_t hi_seg = (need_end - base + L - 1) / L;
-    bool ok = true;
-    while (waited < hi_seg) {  // on a timeout `waited` stays at the segment not seen
-      if (!mbar_wait(bar0 + 8 * (waited % S), (waited / S) & 1u, kOwnerWaitNs, A.status)) {
-        ok = false;
-        break;
+  const uint32_t W_threads = K * Tl;  // the producer is the warp after the groups
+  if (t >= W_threads) {
+    if (lane == 0) {
+      // fill slot i % S with segment i once every group has released segment i - S
+      uint32_t i = 0;
+      for (; i < nseg && !*(volatile int*)&s_bad; ++i) {
+        if (i >= S &&
+            !mbar_wait(empty0 + 8 * (i % S), ((i / S) - 1) & 1u, kOwnerWaitNs, A.status)) {
+          s_bad = 1;
+          break;
+        }
+        const uint32_t lo = base + i * L;
+        const uint32_t len = send - lo < L ? send - lo : L;
+        mbar_expect_tx(full0 + 8 * (i % S), len * 4u);
+        bulk_g2s(ring + (size_t)(i % S) * L, A.in + lo, len * 4u, full0 + 8 * (i % S));
       }
-      ++waited;
+      // no copy may still be landing when the CTA leaves: wait for the last
+      // fill of every slot
+      for (uint32_t j = i > S ? i - S : 0; j < i; ++j)
+        mbar_wait(full0 + 8 * (j % S), (j / S) & 1u, kOwnerWaitNs, nullptr);
     }
-    if (!ok) s_bad = 1;
-    if (ok) {
-      const uint32_t cb = qp & 1u;
-      for (uint32_t g = ga + gr; g < gb; g += K) {  // group gr plays team g
+  } else {
+    const Win W{ring, base, S * L};
+    uint32_t waited = 0;    // every thread: segments [0, waited) seen filled
+    uint32_t released = 0;  // the group's leader: segments [0, released) released
+    uint32_t j = 0;         // the group's team count (dynamic counter parity)
+    // the group's barrier; every member gets the same answer to "has any
+    // member seen the give-up flag", so the group stops as one
+    auto group_sync_stop = [&]() {
+      const bool v = *(volatile int*)&s_bad != 0;
+      if (Tl == 32) {
+        __syncwarp();
+        return __any_sync(0xffffffffu, v) != 0;
+      }
+      return named_barrier_or(1 + gr, Tl, v);
+    };
+    // the leader releases segments [released, upto): each after it is seen
+    // filled, so an arrival always counts for the segment in the slot
+    auto release = [&](uint32_t upto) {
+      if (tt == 0) {
+        for (; released < upto; ++released) {
+          if (!mbar_wait(full0 + 8 * (released % S), (released / S) & 1u, kOwnerWaitNs,
+                         A.status)) {
+            s_bad = 1;
+            break;
+          }
+          mbar_arrive(empty0 + 8 * (released % S));
+        }
+      }
+    };
+    for (uint32_t g = g0 + gr; g < g1; g += K, ++j) {  // group gr plays team g
+      const uint32_t hi_seg = seg_hi(g);
+      if (waited < seg_lo(g)) waited = seg_lo(g);  // segments below are never read here
+      bool ok = !*(volatile int*)&s_bad;
+      while (ok && waited < hi_seg) {
+        if (!mbar_wait(full0 + 8 * (waited % S), (waited / S) & 1u, kOwnerWaitNs, A.status)) {
+          ok = false;
+          s_bad = 1;
+          break;
+        }
+        ++waited;
+      }
+      ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the dynamic claims are warp-wide
+      if (ok) {
         uint32_t bs, bn;
         owner_block(A, g, bs, bn);
         if constexpr (SCHED == kStatic) {
@@ -335,7 +374,7 @@ __global__ void __launch_bounds__(1024) stencil2d_owner_kernel(const OwnerArgs A
         } else {  // kDynamic
           const uint32_t c = A.chunk;
           const uint32_t nch = (uint32_t)(((uint64_t)bn + c - 1) / c);
-          uint32_t* const cp = &ctr[cb][g - ga];
+          uint32_t* const cp = &ctr[gr][j & 1u];
           for (;;) {
             uint32_t b0 = 0;
             if (lane == 0) b0 = atomicAdd(cp, 32u);
@@ -350,29 +389,25 @@ __global__ void __launch_bounds__(1024) stencil2d_owner_kernel(const OwnerArgs A
           }
         }
       }
-      // the counters of pass qp + 1 (last used in pass qp - 1) start at zero
-      if (SCHED == kDynamic && t < kOwnerMaxPassTeams) ctr[cb ^ 1u][t] = 0;
+      // the team is done: its segments are read out, its counter idle
+      const bool stop = group_sync_stop();
+      // this counter serves the team after next; the segments below the next
+      // team's go back to the producer
+      if (SCHED == kDynamic && tt == 0) ctr[gr][j & 1u] = 0;
+      if (stop) break;
+      release(g + K < g1 ? seg_lo(g + K) : nseg);
     }
-    __syncthreads();  // the pass's segments are read out before any slot is refilled
-    if (s_bad) {      // give up on this CTA's remaining passes; let copies in flight land
-      if (t == 0)
-        for (uint32_t i = waited; i < next; ++i)
-          mbar_wait(bar0 + 8 * (i % S), (i / S) & 1u, kOwnerWaitNs, nullptr);
-      break;
-    }
-    // refill every slot whose segment no later pass needs
-    if (t == 0) {
-      const uint32_t keep = qp + 1 < npass ? first_seg(qp + 1) : nseg;
-      for (; next < nseg && next < keep + S; ++next) issue(next);
-    }
+    if (!*(volatile int*)&s_bad) release(nseg);  // what this group will not read any more
   }
+  __syncthreads();
 }
 
 // cudaErrorNotSupported (nothing launched) where this form does not apply:
 // a schedule other than static / static(c) / dynamic(c), nx not a multiple of
 // 4 (a unit would straddle rows), pointers not 16-byte aligned (bulk copies,
-// 128-bit stores), n = 0 or n >= 2^32 (32-bit indices), or a ring of `budget`
-// bytes that cannot hold one team's pass with a segment to spare.
+// 128-bit stores), n = 0 or n >= 2^32 (32-bit indices), teams of 1024 threads
+// (the producer warp needs room), or a ring of `budget` bytes that cannot
+// hold one team's segments with room to spare.
 cudaError_t launch_stencil2d_owner(const void* in, float* out, uint64_t nx, uint64_t ny, int sched,
                                    uint64_t chunk, float c0, float c1, unsigned teams,
                                    unsigned threads, uint32_t budget, int sm_count, int max_smem,
@@ -380,7 +415,7 @@ cudaError_t launch_stencil2d_owner(const void* in, float* out, uint64_t nx, uint
   const uint64_t n = nx * ny;
   if ((sched != kStatic && sched != kChunked && sched != kDynamic) || budget == 0 || nx < 4 ||
       nx % 4 || ny < 1 || n == 0 || n >= (1ull << 32) || teams < 1 || threads < 32 ||
-      threads > 1024 || threads % 32 || (((uintptr_t)in | (uintptr_t)out) & 15))
+      threads > 512 || threads % 32 || (((uintptr_t)in | (uintptr_t)out) & 15))
     return cudaErrorNotSupported;
   if (sched != kStatic && chunk < 1) return cudaErrorNotSupported;
   OwnerArgs a;
@@ -400,19 +435,23 @@ cudaError_t launch_stencil2d_owner(const void* in, float* out, uint64_t nx, uint
   a.c0 = c0;
   a.c1 = c1;
   a.status = status;
+  a.pass_teams = 1;
   // segments of about a row (4 KB .. 16 KB), the ring as many as the budget
-  // holds; a pass of pt teams spans at most (pt maxb + 2 nx + 8) / L + 2
-  // segments; passes leave at least a quarter of the ring (and two
-  // segments) for the copies in flight
+  // holds.  K groups at work on K consecutive teams need about
+  // (K maxb + 2 nx + 8) / L + 2 segments at once (span); K is the largest
+  // that leaves a quarter of the ring (at least two segments) for the fills
+  // in flight, and fits 1024 threads with the producer warp.
   const uint64_t cap = (budget < (uint64_t)max_smem ? budget : (uint64_t)max_smem);
   const uint64_t L = nx < 1024 ? 1024 : nx > 4096 ? 4096 : (nx + 31) / 32 * 32;
   uint64_t S = (cap > 256 ? cap - 256 : 0) / (4 * L);
   if (S > kOwnerMaxSlots) S = kOwnerMaxSlots;
-  auto span = [&](uint64_t pt) { return (pt * maxb + 2 * nx + 8 + L - 1) / L + 1; };
+  auto span = [&](uint64_t kk) { return (kk * maxb + 2 * nx + 8 + L - 1) / L + 1; };
   const uint64_t spare = S / 4 > 2 ? S / 4 : 2;
-  if (S < 2 || span(1) + 1 > S) return cudaErrorNotSupported;
-  uint64_t pt = 1;
-  while (pt < kOwnerMaxPassTeams && span(pt + 1) + spare <= S) ++pt;
+  if (S < 3 || span(1) + 2 > S) return cudaErrorNotSupported;
+  uint64_t K = 1;
+  const uint64_t kmax = (1024 - 32) / threads < kOwnerMaxGroups ? (1024 - 32) / threads
+                                                                 : kOwnerMaxGroups;
+  while (K < kmax && span(K + 1) + spare <= S) ++K;
   a.seg = (uint32_t)L;
   a.slots = (uint32_t)S;
   const size_t smem = (size_t)(S * L * 4 + 128);
@@ -421,22 +460,17 @@ cudaError_t launch_stencil2d_owner(const void* in, float* out, uint64_t nx, uint
                                    : stencil2d_owner_kernel<kDynamic>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // groups: as many teams at once as 1024 threads and the pass allow
-  uint64_t K = 1024 / threads;
-  if (K > pt) K = pt;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)(K * threads), smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)(K * threads + 32), smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorNotSupported;
-  // resident CTAs, and no more teams per pass than a CTA has teams
+  // resident CTAs, and no more groups than a CTA has teams
   uint64_t P = (uint64_t)per_sm * (uint64_t)sm_count;
   if (P > a.G) P = a.G;
-  const uint64_t per_cta = (a.G + P - 1) / P;
-  if (pt > per_cta) pt = per_cta;
-  if (K > pt) K = pt;
+  const uint64_t per_cta = a.G / P;  // every CTA has at least this many teams
+  if (K > per_cta) K = per_cta;
   a.groups = (uint32_t)K;
-  a.pass_teams = (uint32_t)pt;
-  kern<<<(unsigned)P, (unsigned)(K * threads), smem, st>>>(a);
+  kern<<<(unsigned)P, (unsigned)(K * threads + 32), smem, st>>>(a);
   return cudaGetLastError();
 }
 

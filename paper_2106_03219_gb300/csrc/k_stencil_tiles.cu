@@ -68,8 +68,10 @@ __global__ void __launch_bounds__(256) stencil2d_tiles_kernel(const __grid_const
   constexpr uint32_t R = kTileY / W;
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_bad;
+  // box k at box0 + k * kBoxStride, on a 128-byte boundary; addressed from the
+  // shared array itself so that every access compiles to a shared-memory load
   float* const box0 =
-      (float*)(((uintptr_t)rt_dyn_smem + 127) & ~(uintptr_t)127);  // box k at box0 + k * kBoxStride
+      (float*)(rt_dyn_smem + ((128u - (smem_addr(rt_dyn_smem) & 127u)) & 127u));
   const uint32_t t = threadIdx.x, lane = t & 31, w = t >> 5;
   const uint32_t bar0 = smem_addr(&bars[0]);
   if (t == 0) {

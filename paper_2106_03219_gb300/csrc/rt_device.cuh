@@ -96,6 +96,18 @@ __device__ __forceinline__ void team_barrier() { __syncthreads(); }
 __device__ __forceinline__ void named_barrier(uint32_t id, uint32_t count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
+// The same barrier, returning to every participant whether any of them
+// passed v = true (one uniform answer for the sub-team).
+__device__ __forceinline__ bool named_barrier_or(uint32_t id, uint32_t count, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{ .reg .pred p, q; setp.ne.u32 q, %1, 0; bar.red.or.pred p, %2, %3, q; selp.u32 %0, 1, 0, "
+      "p; }"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
 
 // ---------------------------------------------------------------------------
 // Static split without chunk: entity k of P gets q + (k < r) iterations
@@ -308,6 +320,16 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 __device__ __forceinline__ void mbar_init(uint32_t bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// an mbarrier whose phases complete after `count` arrivals
+__device__ __forceinline__ void mbar_init_count(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// one plain arrival (release semantics: the caller's earlier shared-memory
+// reads are ordered before a waiter's later writes)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 // the one arrival of a phase, announcing `bytes` to come from bulk copies
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {

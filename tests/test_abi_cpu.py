@@ -50,6 +50,9 @@ def test_null_context_is_rejected(L):
     assert L.omprt_reduce(None, 0, R.F32, 0, None, 0, None, 0, 0, None) == R.ERR_NOT_INIT
     assert L.omprt_alloc_shared(None, 16) == R.ERR_NOT_INIT
     assert L.omprt_set_stage_bytes(None, 16) == R.ERR_NOT_INIT
+    assert L.omprt_set_stencil_stage_bytes(None, 16) == R.ERR_NOT_INIT
+    assert L.omprt_launch_generic(None, None, 0, C.byref(d), 0, None, 0, 0, None) == \
+        R.ERR_NOT_INIT
     assert L.omprt_finalize(None) == R.ERR_NOT_INIT
     assert L.omprt_sm_count(None) == 0
 

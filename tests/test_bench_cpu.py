@@ -23,7 +23,11 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "GB/s"
     assert d["e2e"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    from oracle import cores
+    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] == cores.host_cores()
     assert d["cpu_baseline"]["value"] == d["value"]
-    assert "workload" in d["config"]
+    one = d["cpu_baseline"]["one_core"]
+    assert one["cores"] == 1 and one["value"] > 0
+    assert "workload" in d["config"] and "4096x4096" in d["config"]["workload"]
 

@@ -2,7 +2,8 @@
 runtime's own timings of 20k loops) picks configurations for loops it has
 never seen (a fresh seed), and the measured total time of its picks is
 compared with the plain heuristic's and with the per-loop best of the 12.
-The model must beat the heuristic on the total."""
+The model must beat the heuristic on the total by more than the spread of
+repeated, interleaved timings."""
 import json
 import os
 
@@ -16,18 +17,26 @@ pytestmark = pytest.mark.gpu
 
 
 def test_learned_beats_heuristic_on_unseen_loops(rt):
+    """800 loops the model has never seen (seed 2).  Each loop's model pick
+    and heuristic pick are timed interleaved (5 of each, medians), and the
+    whole set three times in fresh random orders.  The gain heuristic / model
+    must exceed 1 in every round, and its mean must exceed 1 by more than
+    three standard deviations of the rounds.  The oracle-best of the 12 bounds
+    the model from below."""
     model = learned.Model.load()
     assert model is not None, "no committed cost model"
     buf = learned.LoopBuffers(1 << 24)
     kind, n = learned.make_loops(800, seed=2)
     n = np.minimum(n, 1 << 24)
-    T = learned.time_loops(rt, kind, n, buf, reps=3)
-    rep = learned.evaluate(rt, model, kind, n, T, buf)
+    rep = learned.compare_picks(rt, model, kind, n, buf, reps=5, rounds=3)
     report_dir = os.environ.get("OMPRT_REPORT_DIR")
     if report_dir and os.path.isdir(report_dir):
         json.dump(rep, open(os.path.join(report_dir, "learned_gain.json"), "w"), indent=1)
-    assert rep["model_total_ms"] < rep["heuristic_total_ms"], rep
-    assert rep["model_total_ms"] >= rep["best_total_ms"]
+    assert min(rep["gain_per_round"]) > 1.0, rep
+    assert rep["gain_mean"] - 1.0 > 3.0 * rep["gain_std"], rep
+    T = learned.time_loops(rt, kind[:200], n[:200], buf, reps=3)
+    best = learned.evaluate(rt, model, kind[:200], n[:200], T, buf)
+    assert best["model_total_ms"] >= best["best_total_ms"]
     # with the model removed the runtime falls back to the heuristic
     d, red = learned.loop_desc(int(kind[0]), int(n[0]), buf)
     assert rt.choose_config(d, red is not None) == learned.HEURISTIC
