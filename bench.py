@@ -618,7 +618,7 @@ def run_single_extra(rt, R, torch, inputs, args):
 
 
 def run_single(rt, torch, plan, args):
-    sel = [p for p in plan if args.single in p[0]]
+    sel = [p for p in plan if p[0] == args.single] or [p for p in plan if args.single in p[0]]
     if not sel:
         raise SystemExit("no plan entry matches %r" % args.single)
     stream = torch.cuda.current_stream()
