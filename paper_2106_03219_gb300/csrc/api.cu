@@ -441,12 +441,24 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
     if (e != cudaErrorNotSupported) return from_cuda(e);
     cudaGetLastError();
   }
-  // the staged ring form of the 2-D stencil where it beats the others
+  // static schedules of the 2-D stencil whose owner map repeats row by row:
+  // vertical strips, rows above / at / below in registers (4096^2, alone:
+  // static(8) 0.73 of the copy rate, static 0.73, static(4) 0.67, static(1)
+  // 0.55, against 0.55 / 0.61 / - / 0.42 in the other forms)
+  if (d->body == OMPRT_BODY_STENCIL2D5 && acc == kAccNone && d->data_type == OMPRT_F32 &&
+      (ksched == kStatic || ksched == kChunked)) {
+    e = launch_stencil2d_strips(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny, ksched,
+                                (uint64_t)chunk, (float)d->c0, (float)d->c1, (unsigned)teams,
+                                (unsigned)threads, c->sm_count, st);
+    if (e != cudaErrorNotSupported) return from_cuda(e);
+    cudaGetLastError();
+  }
+  // the streamed ring form of the 2-D stencil where it beats the others
   // (measured at 4096^2, best teams x threads of each form): dynamic(256)
-  // 0.44 of the copy rate against 0.25 plain, static(1) 0.42 against 0.40;
-  // static and static(c > 1) stay with their own forms (static 0.59 plain
-  // against 0.51 staged, static(8) 0.53 against 0.52, static(64) 0.45 in the
-  // row ring against 0.44)
+  // 0.44 of the copy rate against 0.25 plain; static(1) launches that are not
+  // row-periodic 0.42 against 0.40; static and static(c > 1) stay with their
+  // own forms (plain static 0.59 against 0.51 in the ring, static(8) 0.53
+  // against 0.52, static(64) 0.45 in the row ring against 0.44)
   if (d->body == OMPRT_BODY_STENCIL2D5 && acc == kAccNone && d->data_type == OMPRT_F32 &&
       (ksched == kDynamic || (ksched == kChunked && chunk == 1)) &&
       c->stencil_stage_bytes != 0) {

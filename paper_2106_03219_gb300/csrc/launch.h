@@ -57,6 +57,13 @@ cudaError_t launch_stencil2d_owner(const void* in, float* out, uint64_t nx, uint
                                    unsigned threads, uint32_t budget, int sm_count, int max_smem,
                                    uint32_t* status, cudaStream_t st);
 
+// static(1), static(4/8) and static 2-D stencil whose owner map repeats row
+// by row, walked as vertical strips (k_stencil_strips.cu);
+// cudaErrorNotSupported (nothing launched) for other launches.
+cudaError_t launch_stencil2d_strips(const void* in, float* out, uint64_t nx, uint64_t ny, int sched,
+                                    uint64_t chunk, float c0, float c1, unsigned teams,
+                                    unsigned threads, int sm_count, cudaStream_t st);
+
 // Support kernels (k_support.cu).
 cudaError_t launch_static_table(uint64_t n, int64_t lb, int64_t incr, uint64_t chunk, unsigned G,
                                 unsigned T, int64_t* table, cudaStream_t st);
