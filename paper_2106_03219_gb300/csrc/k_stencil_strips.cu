@@ -73,7 +73,9 @@ __device__ __forceinline__ void strip_store(float* p, const float (&v)[W]) {
   }
 }
 
-template <int W, int M>
+// D: rows loaded ahead of the one being computed (the loads of rows r + 2 ..
+// r + 1 + D are in flight while row r computes).
+template <int W, int M, int D>
 __global__ void __launch_bounds__(1024) stencil2d_strips_kernel(const StripArgs A) {
   const uint32_t t = threadIdx.x, T = blockDim.x, lane = t & 31u;
   const uint32_t P = gridDim.x, k = blockIdx.x;
@@ -84,48 +86,56 @@ __global__ void __launch_bounds__(1024) stencil2d_strips_kernel(const StripArgs 
   uint32_t col[M];  // first column of each strip
 #pragma unroll
   for (int m = 0; m < M; ++m) col[m] = (uint32_t)W * (t + (uint32_t)m * T);
-  float up[M][W], cur[M][W], dn[M][W];
-  auto load_row = [&](uint32_t r, float (&v)[M][W]) {
+  // v[0] the row above, v[1] the row being computed, v[2 ..] the rows below
+  float v[D + 2][M][W];
+  auto load_row = [&](uint32_t r, float (&x)[M][W]) {
 #pragma unroll
-    for (int m = 0; m < M; ++m) strip_load<W>(A.in + (size_t)r * nx + col[m], v[m]);
+    for (int m = 0; m < M; ++m) strip_load<W>(A.in + (size_t)r * nx + col[m], x[m]);
   };
-  if (R0 >= 1) load_row(R0 - 1, up);
-  load_row(R0, cur);
-  if (R0 + 1 < ny) load_row(R0 + 1, dn);
+  if (R0 >= 1) load_row(R0 - 1, v[0]);
+  load_row(R0, v[1]);
+#pragma unroll
+  for (int d = 2; d < D + 2; ++d)  // rows R0 + 1 .. R0 + D, those the band reads
+    if (R0 + d - 1 < ny && R0 + d - 2 < R1) load_row(R0 + d - 1, v[d]);
   for (uint32_t r = R0; r < R1; ++r) {
-    float dn2[M][W];
-    const bool more = r + 1 < R1 && r + 2 < ny;  // the next step needs row r + 2
-    if (more) load_row(r + 2, dn2);
+    float nxt[M][W];
+    // row r + 1 + D, needed D steps from now
+    const bool more = r + D < R1 && r + 1 + D < ny;
+    if (more) load_row(r + 1 + D, nxt);
     const bool inner = r >= 1 && r + 1 < ny;
     const size_t row = (size_t)r * nx;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       // west / east of the strip: the neighbouring lanes' edge values; the
       // lanes at a warp's edge read theirs (columns 0 and nx - 1 are copied)
-      float w = __shfl_up_sync(0xffffffffu, cur[m][W - 1], 1);
-      float e = __shfl_down_sync(0xffffffffu, cur[m][0], 1);
+      float w = __shfl_up_sync(0xffffffffu, v[1][m][W - 1], 1);
+      float e = __shfl_down_sync(0xffffffffu, v[1][m][0], 1);
       if (inner && lane == 0 && col[m] > 0) w = __ldg(A.in + row + col[m] - 1);
       if (inner && lane == 31 && col[m] + W < nx) e = __ldg(A.in + row + col[m] + W);
       float o[W];
 #pragma unroll
       for (int q = 0; q < W; ++q) {
         const uint32_t cc = col[m] + q;
-        const float ww = q > 0 ? cur[m][q - 1] : w;
-        const float ee = q + 1 < W ? cur[m][q + 1] : e;
-        o[q] = (inner && cc > 0 && cc + 1 < nx) ? strip_point(A, up[m][q], dn[m][q], ee, ww,
-                                                              cur[m][q])
-                                                : cur[m][q];
+        const float ww = q > 0 ? v[1][m][q - 1] : w;
+        const float ee = q + 1 < W ? v[1][m][q + 1] : e;
+        o[q] = (inner && cc > 0 && cc + 1 < nx)
+                   ? strip_point(A, v[0][m][q], v[2][m][q], ee, ww, v[1][m][q])
+                   : v[1][m][q];
       }
       strip_store<W>(A.out + row + col[m], o);
     }
 #pragma unroll
-    for (int m = 0; m < M; ++m)
+    for (int d = 0; d < D + 1; ++d)
 #pragma unroll
-      for (int q = 0; q < W; ++q) {
-        up[m][q] = cur[m][q];
-        cur[m][q] = dn[m][q];
-        if (more) dn[m][q] = dn2[m][q];
-      }
+      for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < W; ++q) v[d][m][q] = v[d + 1][m][q];
+    if (more) {
+#pragma unroll
+      for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < W; ++q) v[D + 1][m][q] = nxt[m][q];
+    }
   }
 }
 
@@ -165,14 +175,15 @@ cudaError_t launch_stencil2d_strips(const void* in, float* out, uint64_t nx, uin
   a.rows_per_team = (uint32_t)rpt;
   a.c0 = c0;
   a.c1 = c1;
+  // two rows ahead where a thread's row is at most four floats, else one
   void (*kern)(StripArgs) = nullptr;
-  if (W == 1 && M == 1) kern = stencil2d_strips_kernel<1, 1>;
-  if (W == 1 && M == 2) kern = stencil2d_strips_kernel<1, 2>;
-  if (W == 1 && M == 4) kern = stencil2d_strips_kernel<1, 4>;
-  if (W == 1 && M == 8) kern = stencil2d_strips_kernel<1, 8>;
-  if (W == 4 && M == 1) kern = stencil2d_strips_kernel<4, 1>;
-  if (W == 4 && M == 2) kern = stencil2d_strips_kernel<4, 2>;
-  if (W == 8 && M == 1) kern = stencil2d_strips_kernel<8, 1>;
+  if (W == 1 && M == 1) kern = stencil2d_strips_kernel<1, 1, 2>;
+  if (W == 1 && M == 2) kern = stencil2d_strips_kernel<1, 2, 2>;
+  if (W == 1 && M == 4) kern = stencil2d_strips_kernel<1, 4, 2>;
+  if (W == 1 && M == 8) kern = stencil2d_strips_kernel<1, 8, 1>;
+  if (W == 4 && M == 1) kern = stencil2d_strips_kernel<4, 1, 2>;
+  if (W == 4 && M == 2) kern = stencil2d_strips_kernel<4, 2, 1>;
+  if (W == 8 && M == 1) kern = stencil2d_strips_kernel<8, 1, 1>;
   if (!kern) return cudaErrorNotSupported;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, 0);
