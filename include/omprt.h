@@ -236,6 +236,17 @@ omprt_status omprt_set_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_team);
  * memory is OMPRT_ERR_INVALID.  Default after init: 226 KiB. */
 omprt_status omprt_set_stencil_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_cta);
 
+/* The slab form of the 2-D stencil (static(c) and dynamic(c) with c a
+ * multiple of the slab line dividing nx, team blocks of whole rows, and
+ * nx / c a multiple or a divisor of 32; on when stencil stage bytes are
+ * non-zero): each warp takes its 32 chunks in slabs, one tensor copy a slab
+ * (Sec. 3.1's team-shared staging, per warp), every thread running exactly
+ * its own iterations.  slab_floats: floats of each chunk a slab holds, 16 or
+ * 32; buffers: slabs a warp holds, 2 .. 4 (buffers - 1 copies in flight).
+ * 0 for either takes the measured default.  Other values: OMPRT_ERR_INVALID,
+ * nothing changed. */
+omprt_status omprt_set_stencil_slab_shape(omprt_ctx *ctx, int32_t slab_floats, int32_t buffers);
+
 /*
  * Run one "target teams distribute parallel for" region:
  *   level 1: the n logical iterations are split among num_teams teams in

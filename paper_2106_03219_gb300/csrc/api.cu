@@ -234,6 +234,16 @@ omprt_status omprt_set_stage_bytes(omprt_ctx* c, int64_t bytes) {
   return OMPRT_OK;
 }
 
+omprt_status omprt_set_stencil_slab_shape(omprt_ctx* c, int32_t slab_floats, int32_t buffers) {
+  if (!c) return OMPRT_ERR_NOT_INIT;
+  if ((slab_floats != 0 && slab_floats != 16 && slab_floats != 32) ||
+      (buffers != 0 && (buffers < 2 || buffers > 4)))
+    return OMPRT_ERR_INVALID;
+  c->slab_floats = (uint32_t)slab_floats;
+  c->slab_buffers = (uint32_t)buffers;
+  return OMPRT_OK;
+}
+
 omprt_status omprt_set_stencil_stage_bytes(omprt_ctx* c, int64_t bytes) {
   if (!c) return OMPRT_ERR_NOT_INIT;
   if (bytes < 0 || bytes > (int64_t)c->max_smem_optin) return OMPRT_ERR_INVALID;
@@ -441,6 +451,19 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
     if (e != cudaErrorNotSupported) return from_cuda(e);
     cudaGetLastError();
   }
+  // static(c) and dynamic(c) with c a multiple of 16 dividing nx and team
+  // blocks of whole rows: each warp's chunks in swizzled tensor-copied slabs
+  // (4096^2, alone: static(64) 0.73 of the copy rate, dynamic(64) 0.70,
+  // dynamic(256) 0.62, against 0.46 / - / 0.44 in the forms below)
+  if (d->body == OMPRT_BODY_STENCIL2D5 && acc == kAccNone && d->data_type == OMPRT_F32 &&
+      (ksched == kDynamic || ksched == kChunked) && c->stencil_stage_bytes != 0) {
+    e = launch_stencil2d_slabs(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny, ksched,
+                               (uint64_t)chunk, (float)d->c0, (float)d->c1, (unsigned)teams,
+                               (unsigned)threads, c->slab_floats, c->slab_buffers, c->sm_count,
+                               c->max_smem_optin, c->status_dev, st);
+    if (e != cudaErrorNotSupported) return from_cuda(e);
+    cudaGetLastError();
+  }
   // static schedules of the 2-D stencil whose owner map repeats row by row:
   // vertical strips, rows above / at / below in registers (4096^2, alone:
   // static(8) 0.73 of the copy rate, static 0.73, static(4) 0.67, static(1)
@@ -450,6 +473,18 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
     e = launch_stencil2d_strips(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny, ksched,
                                 (uint64_t)chunk, (float)d->c0, (float)d->c1, (unsigned)teams,
                                 (unsigned)threads, c->sm_count, st);
+    if (e != cudaErrorNotSupported) return from_cuda(e);
+    cudaGetLastError();
+  }
+  // dynamic(c) outside the slab form, team blocks of whole rows: the row
+  // ring (4096^2 dynamic(256): 0.47 of the copy rate against 0.44 in the
+  // streamed ring below)
+  if (d->body == OMPRT_BODY_STENCIL2D5 && acc == kAccNone && d->data_type == OMPRT_F32 &&
+      ksched == kDynamic && c->stencil_stage_bytes != 0) {
+    e = launch_stencil2d_rowring(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny, ksched,
+                                 (uint64_t)chunk, (float)d->c0, (float)d->c1, (unsigned)teams,
+                                 (unsigned)threads, c->stencil_stage_bytes, c->sm_count,
+                                 c->max_smem_optin, c->status_dev, st);
     if (e != cudaErrorNotSupported) return from_cuda(e);
     cudaGetLastError();
   }

@@ -19,6 +19,8 @@ struct omprt_ctx {
   uint32_t stack_bytes = 0;
   uint32_t stage_bytes = 32768;    // per-team shared memory for staged dynamic schedules
   uint32_t stencil_stage_bytes = 0;  // per-CTA shared memory for the staged 2-D stencil windows
+  uint32_t slab_floats = 0;   // 2-D stencil slabs: floats a line (16 / 32; 0 the default)
+  uint32_t slab_buffers = 0;  // and buffers a warp (2 .. 4; 0 the default)
   std::atomic<uint32_t> next_slot{0};
   // learned schedule (host copy of the model)
   bool has_model = false;

@@ -236,13 +236,10 @@ extern "C" omprt_status omprt_launch_generic(omprt_ctx* c, const int64_t* seg_de
   a.pool = c->pool_dev;
   a.result = result_dev;
   a.status = c->status_dev;
-  if (a.stack_bytes > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.stack_bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return OMPRT_ERR_CUDA;
-    }
+  static const size_t static_bytes = static_smem_of(generic_kernel);
+  if (smem_optin(generic_kernel, a.stack_bytes, static_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return OMPRT_ERR_CUDA;
   }
   generic_kernel<<<teams, threads, a.stack_bytes, (cudaStream_t)stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? OMPRT_OK : OMPRT_ERR_CUDA;

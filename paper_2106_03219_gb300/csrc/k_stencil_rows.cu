@@ -211,11 +211,9 @@ cudaError_t launch_stencil2d_rows(const void* in, float* out, uint64_t nx, uint6
   a.K = 2;
   const uint64_t smem = (2ull * a.K + 2) * slot_bytes;
   if (smem + 2048 > (uint64_t)max_smem) return cudaErrorNotSupported;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(stencil2d_rows_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  static const size_t static_bytes = static_smem_of(stencil2d_rows_kernel);
+  const cudaError_t e = smem_optin(stencil2d_rows_kernel, smem, static_bytes);
+  if (e != cudaSuccess) return e;
   stencil2d_rows_kernel<<<teams, threads, smem, st>>>(a);
   return cudaGetLastError();
 }

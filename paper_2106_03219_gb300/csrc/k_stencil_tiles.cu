@@ -16,9 +16,7 @@
 // columns west and east of the strip come from the neighbouring lanes by
 // shuffle.  Stores are 128-bit and coalesced (a warp writes 512 contiguous
 // bytes per row).  The arithmetic is the body's: fma(c1, (N+S)+(E+W), c0*C).
-#include <cuda.h>  // CUtensorMap and its enums (types only; no driver library is linked)
-
-#include "api_internal.h"
+#include "tensor_map.h"
 
 namespace rt {
 
@@ -142,16 +140,9 @@ __global__ void __launch_bounds__(256) stencil2d_tiles_kernel(const __grid_const
   }
 }
 
-// cuTensorMapEncodeTiled, looked up once through the runtime's driver entry
-// point query (the driver library is not linked).
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 // The driver's entry point is process-wide: looked up once, by the first
 // caller (a function-local static is initialised exactly once, thread-safely).
-static EncodeTiledFn encode_tiled() {
+EncodeTiledFn encode_tiled() {
   static const EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -209,7 +200,7 @@ cudaError_t launch_stencil2d_tiles(const void* in, float* out, uint64_t nx, uint
                             : stencil2d_tiles_kernel<1>;
   // the opt-in is a property of the kernel on the current device, so it is
   // set at every launch (as for the region kernels), not cached per process
-  if (kTileSmem > 48 * 1024) {
+  {
     const cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
     if (e != cudaSuccess) return e;

@@ -172,11 +172,9 @@ __global__ void test_stack_kernel(uint32_t S, uint32_t Q, unsigned char* pool, c
 cudaError_t launch_test_stack(unsigned G, uint32_t S, uint32_t Q, unsigned char* pool,
                               const int64_t* ops, int64_t nops, int64_t* out, int64_t* status_out,
                               uint32_t* status, cudaStream_t st) {
-  if (S > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(test_stack_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S);
-    if (e != cudaSuccess) return e;
-  }
+  static const size_t static_bytes = static_smem_of(test_stack_kernel);
+  const cudaError_t e = smem_optin(test_stack_kernel, S, static_bytes);
+  if (e != cudaSuccess) return e;
   test_stack_kernel<<<G, 32, S, st>>>(S, Q, pool, ops, nops, out, status_out, status);
   return cudaGetLastError();
 }

@@ -7,6 +7,24 @@
 
 namespace rt {
 
+// A launch gets 48 KB of shared memory, static and dynamic together, without
+// the kernel's opt-in; beyond that the opt-in must cover the dynamic part.
+// The kernel's static part is looked up once per kernel by the caller.
+template <class K>
+inline size_t static_smem_of(K kern) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+    cudaGetLastError();
+    return 48 * 1024;  // unknown: always opt in
+  }
+  return fa.sharedSizeBytes;
+}
+template <class K>
+inline cudaError_t smem_optin(K kern, size_t dyn, size_t static_bytes) {
+  if (dyn + static_bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 // Reduction accumulator selected for a launch.
 enum AccKind : int {
   kAccNone = 0,
@@ -56,6 +74,26 @@ cudaError_t launch_stencil2d_owner(const void* in, float* out, uint64_t nx, uint
                                    uint64_t chunk, float c0, float c1, unsigned teams,
                                    unsigned threads, uint32_t budget, int sm_count, int max_smem,
                                    uint32_t* status, cudaStream_t st);
+
+// static(c) and dynamic(c) 2-D stencil, c a multiple of 32 dividing nx, team
+// blocks of whole rows: each warp's chunks arrive slab by slab as swizzled
+// tensor copies (k_stencil_slabs.cu); cudaErrorNotSupported (nothing
+// launched) for other launches.
+cudaError_t launch_stencil2d_slabs(const void* in, float* out, uint64_t nx, uint64_t ny, int sched,
+                                   uint64_t chunk, float c0, float c1, unsigned teams,
+                                   unsigned threads, uint32_t slab_floats, uint32_t buffers,
+                                   int sm_count, int max_smem, uint32_t* status,
+                                   cudaStream_t st);
+
+// dynamic(c) 2-D stencil, team blocks of whole rows, streamed through a ring
+// of row slots in shared memory, `budget` bytes per CTA
+// (k_stencil_rowring.cu); cudaErrorNotSupported (nothing launched) for other
+// launches.
+cudaError_t launch_stencil2d_rowring(const void* in, float* out, uint64_t nx, uint64_t ny,
+                                     int sched, uint64_t chunk, float c0, float c1,
+                                     unsigned teams, unsigned threads, uint32_t budget,
+                                     int sm_count, int max_smem, uint32_t* status,
+                                     cudaStream_t st);
 
 // static(1), static(4/8) and static 2-D stencil whose owner map repeats row
 // by row, walked as vertical strips (k_stencil_strips.cu);

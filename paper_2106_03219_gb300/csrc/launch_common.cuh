@@ -9,10 +9,9 @@ template <class Body, class Acc, int SCHED>
 inline cudaError_t launch_one(unsigned grid, unsigned block, size_t smem, cudaStream_t st,
                               const RegionArgs& a) {
   auto k = region_kernel<Body, SCHED, Acc>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  static const size_t static_bytes = static_smem_of(k);
+  const cudaError_t e = smem_optin(k, smem, static_bytes);
+  if (e != cudaSuccess) return e;
   k<<<grid, block, smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -69,6 +69,7 @@ def _declare(L):
         "omprt_alloc_shared": (st, [vp, C.c_size_t]),
         "omprt_set_stage_bytes": (st, [vp, i64]),
         "omprt_set_stencil_stage_bytes": (st, [vp, i64]),
+        "omprt_set_stencil_slab_shape": (st, [vp, i32, i32]),
         "omprt_launch_region": (st, [vp, C.POINTER(LoopDesc), i32, i64, i32, i32,
                                      C.POINTER(ReduceDesc), vp]),
         "omprt_launch_region_dist": (st, [vp, C.POINTER(LoopDesc), i64, i32, i64, i32, i32,
@@ -215,6 +216,12 @@ class Runtime:
     def set_stage_bytes(self, nbytes):
         """Per-team shared memory for staged dynamic schedules (0: plain form)."""
         check(lib().omprt_set_stage_bytes(self.ctx, int(nbytes)), "omprt_set_stage_bytes")
+
+    def set_stencil_slab_shape(self, slab_floats=0, buffers=0):
+        """omprt_set_stencil_slab_shape: floats a slab line (16 / 32) and slabs a
+        warp (2 .. 4) of the 2-D stencil's slab form; 0 the default."""
+        check(lib().omprt_set_stencil_slab_shape(self.ctx, int(slab_floats), int(buffers)),
+              "omprt_set_stencil_slab_shape")
 
     def set_stencil_stage_bytes(self, nbytes):
         """omprt_set_stencil_stage_bytes: per-CTA shared memory for the staged 2-D
