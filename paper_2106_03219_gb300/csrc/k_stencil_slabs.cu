@@ -41,7 +41,10 @@ namespace rt {
 constexpr uint32_t kSlabMaxWarps = 16;
 constexpr uint32_t kSlabMaxTeams = 1024;  // per CTA: the dynamic counters
 constexpr uint64_t kSlabWaitNs = 1000000000ull;  // 1 s: a slab takes microseconds
-constexpr uint32_t kSlabDefaultFloats = 32, kSlabDefaultBuffers = 2;
+// defaults: 32-float lines, and about 24 KB of slab buffers a warp (4096^2:
+// 12 KB boxes best with 2 buffers, static(64) 0.73 against 0.72 with 3;
+// 8 KB boxes with 3, dynamic(256) 0.64 against 0.54 with 2)
+constexpr uint32_t kSlabDefaultFloats = 32, kSlabWarpBytes = 24 * 1024;
 
 struct SlabArgs {
   const float* in;
@@ -303,8 +306,7 @@ cudaError_t launch_stencil2d_slabs(const void* in, float* out, uint64_t nx, uint
                                    cudaStream_t st) {
   const uint64_t n = nx * ny;
   const uint32_t X = slab_floats ? slab_floats : (chunk % 32 ? 16u : kSlabDefaultFloats);
-  const uint32_t NB = buffers ? buffers : kSlabDefaultBuffers;
-  if ((sched != kChunked && sched != kDynamic) || (X != 16 && X != 32) || NB < 2 || NB > 4 ||
+  if ((sched != kChunked && sched != kDynamic) || (X != 16 && X != 32) ||
       nx < X || ny < 1 || n >= (1ull << 32) || chunk < X || chunk % X || nx % chunk ||
       teams < 1 || teams > ny || ny % teams || threads < 32 || threads % 32 ||
       threads > kSlabMaxWarps * 32 || (((uintptr_t)in | (uintptr_t)out) & 15))
@@ -329,6 +331,9 @@ cudaError_t launch_stencil2d_slabs(const void* in, float* out, uint64_t nx, uint
   a.nch = a.R * a.m;
   a.box_bytes = 4u * X * a.mb * a.nr;
   a.slab = (a.box_bytes + 1023u) & ~1023u;
+  uint32_t NB = buffers ? buffers : kSlabWarpBytes / a.slab;
+  if (NB < 2) NB = 2;
+  if (NB > 4) NB = 4;
   a.c0 = c0;
   a.c1 = c1;
   a.status = status;
@@ -366,9 +371,12 @@ cudaError_t launch_stencil2d_slabs(const void* in, float* out, uint64_t nx, uint
   if (per_sm < 1) return cudaErrorNotSupported;
   uint64_t P = (uint64_t)per_sm * (uint64_t)sm_count;
   if (P > teams) P = teams;
-  const uint64_t per_cta = teams / P;  // every CTA has at least this many teams
-  if (K > per_cta) K = per_cta;
-  if (sched == kDynamic && (teams + P - 1) / P > kSlabMaxTeams) return cudaErrorNotSupported;
+  // groups beyond a CTA's teams idle: with K groups a CTA of ceil(G / P)
+  // teams takes ceil(ceil(G / P) / K) rounds, so K is not cut down to the
+  // smaller CTAs' count (that would give the larger ones a second round)
+  const uint64_t per_cta_max = (teams + P - 1) / P;
+  if (K > per_cta_max) K = per_cta_max;
+  if (sched == kDynamic && per_cta_max > kSlabMaxTeams) return cudaErrorNotSupported;
   a.K = (uint32_t)K;
   kern<<<(unsigned)P, (unsigned)(K * threads), smem, st>>>(map, a);
   return cudaGetLastError();
