@@ -243,8 +243,10 @@ omprt_status omprt_set_stencil_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_cta
  * (Sec. 3.1's team-shared staging, per warp), every thread running exactly
  * its own iterations.  slab_floats: floats of each chunk a slab holds, 16 or
  * 32; buffers: slabs a warp holds, 2 .. 4 (buffers - 1 copies in flight).
- * 0 for either takes the measured default.  Other values: OMPRT_ERR_INVALID,
- * nothing changed. */
+ * buffers also sets the band form of static(1) (team size dividing nx, team
+ * blocks of whole rows: each warp's strips a band of rows at a time from
+ * tensor copies).  0 for either takes the measured default (bands: 2).
+ * Other values: OMPRT_ERR_INVALID, nothing changed. */
 omprt_status omprt_set_stencil_slab_shape(omprt_ctx *ctx, int32_t slab_floats, int32_t buffers);
 
 /*

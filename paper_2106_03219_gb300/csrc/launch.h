@@ -95,6 +95,15 @@ cudaError_t launch_stencil2d_rowring(const void* in, float* out, uint64_t nx, ui
                                      int sm_count, int max_smem, uint32_t* status,
                                      cudaStream_t st);
 
+// static(1) 2-D stencil, team size dividing nx, team blocks of whole rows:
+// each warp's strips a band of rows at a time from tensor copies
+// (k_stencil_bands.cu); cudaErrorNotSupported (nothing launched) for other
+// launches.
+cudaError_t launch_stencil2d_bands(const void* in, float* out, uint64_t nx, uint64_t ny, float c0,
+                                   float c1, unsigned teams, unsigned threads, uint32_t buffers,
+                                   int sm_count, int max_smem, uint32_t* status,
+                                   cudaStream_t st);
+
 // static(1), static(4/8) and static 2-D stencil whose owner map repeats row
 // by row, walked as vertical strips (k_stencil_strips.cu);
 // cudaErrorNotSupported (nothing launched) for other launches.
