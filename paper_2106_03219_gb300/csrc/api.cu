@@ -451,6 +451,18 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
     if (e != cudaErrorNotSupported) return from_cuda(e);
     cudaGetLastError();
   }
+  // teams of one warp whose blocks are several rows of one 32-chunk group
+  // (m = nx / c < 32): the CTA's warps on adjacent teams, one tensor copy a
+  // step for all of them (4096^2 dynamic(256): 0.68 against 0.65 in slabs)
+  if (d->body == OMPRT_BODY_STENCIL2D5 && acc == kAccNone && d->data_type == OMPRT_F32 &&
+      (ksched == kDynamic || ksched == kChunked) && c->stencil_stage_bytes != 0) {
+    e = launch_stencil2d_colring(d->x, (float*)d->out, (uint64_t)d->nx, (uint64_t)d->ny, ksched,
+                                 (uint64_t)chunk, (float)d->c0, (float)d->c1, (unsigned)teams,
+                                 (unsigned)threads, c->slab_buffers, c->sm_count,
+                                 c->max_smem_optin, c->status_dev, st);
+    if (e != cudaErrorNotSupported) return from_cuda(e);
+    cudaGetLastError();
+  }
   // static(c) and dynamic(c) with c a multiple of 16 dividing nx and team
   // blocks of whole rows: each warp's chunks in swizzled tensor-copied slabs
   // (4096^2, alone: static(64) 0.73 of the copy rate, dynamic(64) 0.70,

@@ -75,6 +75,16 @@ cudaError_t launch_stencil2d_owner(const void* in, float* out, uint64_t nx, uint
                                    unsigned threads, uint32_t budget, int sm_count, int max_smem,
                                    uint32_t* status, cudaStream_t st);
 
+// static(c) and dynamic(c) 2-D stencil with teams of one warp whose blocks are
+// the 32 / m rows that hold 32 chunks (m = nx / c < 32): the CTA's warps play
+// adjacent teams, one tensor copy a step for all of them (k_stencil_colring.cu); cudaErrorNotSupported
+// (nothing launched) for other launches.
+cudaError_t launch_stencil2d_colring(const void* in, float* out, uint64_t nx, uint64_t ny,
+                                     int sched, uint64_t chunk, float c0, float c1,
+                                     unsigned teams, unsigned threads, uint32_t buffers,
+                                     int sm_count, int max_smem, uint32_t* status,
+                                     cudaStream_t st);
+
 // static(c) and dynamic(c) 2-D stencil, c a multiple of 32 dividing nx, team
 // blocks of whole rows: each warp's chunks arrive slab by slab as swizzled
 // tensor copies (k_stencil_slabs.cu); cudaErrorNotSupported (nothing
