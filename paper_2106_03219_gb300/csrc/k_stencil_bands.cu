@@ -55,14 +55,19 @@ __device__ __forceinline__ float lds32_at(uint32_t addr) {
   return v;
 }
 
+// M strips a thread (a constant, so a thread's per-strip state is registers):
+// the rows above and at the current one ride in registers down the band,
+// each point reads the row below and its west / east words.
+template <int M>
 __global__ void __launch_bounds__(1024) stencil2d_bands_kernel(
     const __grid_constant__ CUtensorMap map, const BandArgs A) {
   __shared__ __align__(8) uint64_t bars[32][kBandMaxNB];
   const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5, T = blockDim.x;
-  const uint32_t NB = A.NB, M = A.M, Rb = A.Rb;
+  const uint32_t NB = A.NB, Rb = A.Rb;
   // buffers on a 128-byte boundary (a tensor copy's destination)
   const uint32_t bufs = (smem_addr(rt_dyn_smem) + 127u) & ~127u;
-  const uint32_t wbytes = M * A.strip_bytes;  // one band of this warp
+  const uint32_t sb = A.strip_bytes;
+  const uint32_t wbytes = M * sb;  // one band of this warp
   const uint32_t buf0 = bufs + w * NB * wbytes;
   const uint32_t bar0 = smem_addr(&bars[w][0]);
   if (lane == 0)
@@ -79,12 +84,21 @@ __global__ void __launch_bounds__(1024) stencil2d_bands_kernel(
     mbar_expect_tx(bar, M * A.box_bytes);
     const uint32_t dst = buf0 + slot * wbytes;
     const int y = (int)(R0 + b * Rb) - 1;
-    for (uint32_t m = 0; m < M; ++m)
-      tma_load_2d(dst + m * A.strip_bytes, &map, (int)(32u * w + m * T) - 4, y, bar);
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+      tma_load_2d(dst + m * sb, &map, (int)(32u * w + m * T) - 4, y, bar);
   };
+  // per strip: is this lane's column interior (not 0, not nx - 1)
+  bool in_col[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const uint32_t col = 32u * w + lane + m * T;
+    in_col[m] = col > 0 && col + 1 < nx;
+  }
   if (lane == 0)
     for (uint32_t b = 0; b + 1 < NB && b < nb; ++b) issue(b, b);
   uint32_t phase = 0;  // bit i: parity of buffer i's next completion
+  constexpr uint32_t kRow = 4u * kBandLine;  // bytes a box row
   for (uint32_t b = 0; b < nb; ++b) {
     const uint32_t slot = b % NB;
     // the band NB - 1 ahead goes to the buffer read out in the previous trip
@@ -101,23 +115,31 @@ __global__ void __launch_bounds__(1024) stencil2d_bands_kernel(
     }
     phase ^= 1u << slot;
     const uint32_t rb0 = R0 + b * Rb, rb1 = rb0 + Rb < R1 ? rb0 + Rb : R1;
-    // word 4 + l of box row j of strip m: box + m strip_bytes + 4 (40 j + 4 + l)
+    // word 4 + l of box row 0 of strip 0; strip m is m sb further
     const uint32_t lw = buf0 + slot * wbytes + 4u * (4u + lane);
-    for (uint32_t r = rb0; r < rb1; ++r) {
-      const uint32_t j = r - rb0 + 1;  // the box row of grid row r
+    float up[M], cu[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      up[m] = lds32_at(lw + m * sb);
+      cu[m] = lds32_at(lw + m * sb + kRow);
+    }
+    uint32_t a = lw + kRow;  // box row of grid row r, strip 0
+    float* orow = A.out + (size_t)rb0 * nx + 32u * w + lane;
+    for (uint32_t r = rb0; r < rb1; ++r, a += kRow, orow += nx) {
       const bool inner = r >= 1 && r + 1 < ny;
-      float* const orow = A.out + (size_t)r * nx + 32u * w + lane;
-      for (uint32_t m = 0; m < M; ++m) {
-        const uint32_t a = lw + m * A.strip_bytes + 4u * kBandLine * j;
-        const float c = lds32_at(a);
-        float o = c;
-        const uint32_t col = 32u * w + lane + m * T;
-        if (inner && col > 0 && col + 1 < nx) {
-          const float nn = lds32_at(a - 4u * kBandLine), ss = lds32_at(a + 4u * kBandLine);
-          const float we = lds32_at(a - 4u), ea = lds32_at(a + 4u);
-          o = __fmaf_rn(A.c1, __fadd_rn(__fadd_rn(nn, ss), __fadd_rn(ea, we)), __fmul_rn(A.c0, c));
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const uint32_t am = a + m * sb;
+        const float dn = lds32_at(am + kRow);
+        float o = cu[m];
+        if (inner && in_col[m]) {
+          const float we = lds32_at(am - 4u), ea = lds32_at(am + 4u);
+          o = __fmaf_rn(A.c1, __fadd_rn(__fadd_rn(up[m], dn), __fadd_rn(ea, we)),
+                        __fmul_rn(A.c0, cu[m]));
         }
         orow[m * T] = o;
+        up[m] = cu[m];
+        cu[m] = dn;
       }
     }
     __syncwarp();  // buffer `slot` is read out before a later trip refills it
@@ -125,7 +147,8 @@ __global__ void __launch_bounds__(1024) stencil2d_bands_kernel(
 }
 
 // cudaErrorNotSupported (nothing launched) unless: n < 2^32, nx a multiple
-// of 4 and of the team size, teams dividing ny, whole warps, the input
+// of 4 and of the team size with nx / T in {1, 2, 4, 8, 16}, teams dividing
+// ny, whole warps, the input
 // 16-byte aligned (a tensor copy's source), buffers in 2 .. 4 (0: 2), room in
 // shared memory for at least one row a band, and a tensor-map encoder.
 cudaError_t launch_stencil2d_bands(const void* in, float* out, uint64_t nx, uint64_t ny, float c0,
@@ -151,8 +174,15 @@ cudaError_t launch_stencil2d_bands(const void* in, float* out, uint64_t nx, uint
   a.c0 = c0;
   a.c1 = c1;
   a.status = status;
+  void (*kern)(const CUtensorMap, const BandArgs) = nullptr;
+  if (a.M == 1) kern = stencil2d_bands_kernel<1>;
+  if (a.M == 2) kern = stencil2d_bands_kernel<2>;
+  if (a.M == 4) kern = stencil2d_bands_kernel<4>;
+  if (a.M == 8) kern = stencil2d_bands_kernel<8>;
+  if (a.M == 16) kern = stencil2d_bands_kernel<16>;
+  if (!kern) return cudaErrorNotSupported;
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, stencil2d_bands_kernel);
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
   const uint64_t room = (uint64_t)max_smem > fa.sharedSizeBytes + 128
                             ? (uint64_t)max_smem - fa.sharedSizeBytes - 128
@@ -177,17 +207,15 @@ cudaError_t launch_stencil2d_bands(const void* in, float* out, uint64_t nx, uint
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorNotSupported;
   const size_t smem = (size_t)(per_rowset * a.strip_bytes + 128);
-  e = cudaFuncSetAttribute(stencil2d_bands_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil2d_bands_kernel, (int)threads,
-                                                    smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorNotSupported;
   uint64_t P = (uint64_t)per_sm * (uint64_t)sm_count;
   if (P > teams) P = teams;
-  stencil2d_bands_kernel<<<(unsigned)P, threads, smem, st>>>(map, a);
+  kern<<<(unsigned)P, threads, smem, st>>>(map, a);
   return cudaGetLastError();
 }
 
