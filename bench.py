@@ -648,7 +648,8 @@ def measure_reductions(rt, R, torch, inputs, n=1 << 28, reps=5):
     (compensated fp32, fp64 combine), 4 teams per SM x 512 threads; inputs
     (0.5-2 GB) are larger than L2.  The fp sums are also run at the two
     comparison precisions (compensated fp32 with an fp32 combine, plain fp32)
-    for the error report.  Returns (per-result dict, host arrays)."""
+    for the error report.  Three warm-up launches, then the mean of `reps`.
+    Returns (per-result dict, host arrays)."""
     out, arrays = {}, {}
     sms = rt.sm_count
     res = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -667,7 +668,8 @@ def measure_reductions(rt, R, torch, inputs, n=1 << 28, reps=5):
         ops = [(name, op)] if name != "fp32_pm1_sum" else [(name, op), ("fp32_max", R.OP_MAX),
                                                            ("fp32_min", R.OP_MIN)]
         for label, o in ops:
-            rt.reduce(o, t, r, R.PREC_COMP_F64, 4 * sms, 512)
+            for _ in range(3):  # warm-up
+                rt.reduce(o, t, r, R.PREC_COMP_F64, 4 * sms, 512)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
