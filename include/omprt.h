@@ -232,8 +232,11 @@ omprt_status omprt_set_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_team);
  * nx is a multiple of 4, n < 2^32, both pointers are 16-byte aligned,
  * thread_limit <= 512 and the ring holds one team's rows with room to spare;
  * other launches run the forms of omprt_set_stage_bytes.  bytes is rounded
- * down to 16; 0 turns this form off; more than the device's per-block shared
- * memory is OMPRT_ERR_INVALID.  Default after init: 226 KiB. */
+ * down to 16; 0 turns this form off, and with it the slab, band, column-ring
+ * and row-ring forms of omprt_set_stencil_slab_shape and the row ring of
+ * dynamic(c) (those size their buffers from the device's shared memory);
+ * more than the device's per-block shared memory is OMPRT_ERR_INVALID.
+ * Default after init: 226 KiB. */
 omprt_status omprt_set_stencil_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_cta);
 
 /* The slab form of the 2-D stencil (static(c) and dynamic(c) with c a
@@ -245,8 +248,11 @@ omprt_status omprt_set_stencil_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_cta
  * 32; buffers: slabs a warp holds, 2 .. 4 (buffers - 1 copies in flight).
  * buffers also sets the band form of static(1) (team size dividing nx, team
  * blocks of whole rows: each warp's strips a band of rows at a time from
- * tensor copies).  0 for either takes the measured default (bands: 2).
- * Other values: OMPRT_ERR_INVALID, nothing changed. */
+ * tensor copies) and the column ring (teams of 32 threads whose blocks are
+ * the 32 / m rows holding 32 chunks, m = nx / c < 32: the CTA's warps play
+ * adjacent teams from one tensor copy a step).  0 for either takes the
+ * measured default (slabs: about 24 KB of buffers a warp; bands: 2; column
+ * ring: 3).  Other values: OMPRT_ERR_INVALID, nothing changed. */
 omprt_status omprt_set_stencil_slab_shape(omprt_ctx *ctx, int32_t slab_floats, int32_t buffers);
 
 /*

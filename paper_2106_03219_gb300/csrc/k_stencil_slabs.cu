@@ -1,28 +1,29 @@
 // The 2-D 5-point stencil under static(c) and dynamic(c) when c is a
-// multiple of 32 that divides nx, every team's block is whole rows (G
-// divides ny), and m = nx / c (chunks per row) is a multiple or a divisor
-// of 32.  The chunks a warp holds at one time arrive, 32 floats of each at a
-// time, as one tensor copy.
+// multiple of the slab line X (16 or 32 floats) that divides nx, every team's
+// block is whole rows (G divides ny), and m = nx / c (chunks per row) is a
+// multiple or a divisor of 32.  The chunks a warp holds at one time arrive,
+// X floats of each at a time, as one tensor copy.
 //
 // The grid is read as a 3-D tensor: x the c floats of a chunk, y the m
 // chunks of a row, z the rows.  A warp holds 32 consecutive chunks of a team
 // block starting at a multiple of 32: with m >= 32 they are chunks y0 .. y0 +
 // 31 of one row, with m < 32 they are 32 / m whole rows.  Slab s of them is
-// the box x in [32 s, 32 s + 32) over those chunks and their rows plus one
-// row above and one below: nr = 32 / mb + 2 rows of mb = min(m, 32) chunks,
-// mb nr lines of 128 bytes, copied with the 128-byte swizzle (in line L of a
-// box, 16-byte unit k sits at unit k ^ (L mod 8)).  Lane l's chunk has its
-// row in line l + mb, the row above in line l and the row below in line l +
-// 2 mb, so when every lane reads unit k of its own chunk the eight lanes of
-// an access phase read eight consecutive lines: distinct bank groups.
+// the box x in [X s, X s + X) over those chunks and their rows plus one row
+// above and one below: nr = 32 / mb + 2 rows of mb = min(m, 32) chunks, mb nr
+// lines of 4 X bytes, copied with the swizzle of the line's width (128-byte
+// lines: 16-byte unit k of line L sits at unit k ^ (L mod 8); 64-byte lines:
+// at k ^ ((L / 2) mod 4)).  Lane l's chunk has its row in line l + mb, the row
+// above in line l and the row below in line l + 2 mb, so when every lane
+// reads unit k of its own chunk the eight lanes of an access phase read
+// eight consecutive lines: distinct bank groups.
 //
-// Every warp runs its own pipeline: two slab buffers, two mbarriers, and
-// lane 0 issuing the copy of the warp's next slab before the lanes compute
-// the current one.  A launch has P <= G resident CTAs; CTA k plays the
-// consecutive teams [k G / P, (k + 1) G / P) (OpenMP does not make teams run
-// at the same time).  Its W warps form K = W / (T / 32) groups; group gr
-// plays the CTA's teams gr, gr + K, ... in turn, its warp i as threads
-// 32 i .. 32 i + 31 of the team.
+// Every warp runs its own pipeline: NB slab buffers with an mbarrier each,
+// lane 0 keeping NB - 1 copies of the warp's next slabs in flight while the
+// lanes compute the current one.  A launch has P <= G resident CTAs; CTA k
+// plays the consecutive teams [k G / P, (k + 1) G / P) (OpenMP does not make
+// teams run at the same time).  Its W warps form K = W / (T / 32) groups;
+// group gr plays the CTA's teams gr, gr + K, ... in turn, its warp i as
+// threads 32 i .. 32 i + 31 of the team.
 //   static(c):  warp i's lanes run chunks j0 + l of the block for j0 = 32 i,
 //               32 i + T, ... (thread tt runs chunks tt, tt + T, ...: C2);
 //   dynamic(c): lane 0 claims 32 chunks with one atomic add on the team's
@@ -30,10 +31,10 @@
 //               runs chunk base + l; a thread's claims increase (C4).
 // A lane runs its chunk slab by slab and each slab unit by unit, in order.
 // Its west neighbour at a chunk's first column and its east neighbour at a
-// slab's last column are read from global memory; the others are carried
-// from unit to unit.  Boundary rows and columns copy their input; the
-// arithmetic is the body's fma(c1, (N+S)+(E+W), c0*C).  Outputs leave two
-// units (32 bytes) a store.
+// slab's last column are read from global memory one slab ahead; the others
+// are carried from unit to unit.  Boundary rows and columns copy their
+// input; the arithmetic is the body's fma(c1, (N+S)+(E+W), c0*C).  Outputs
+// leave two units (32 bytes) a store.
 #include "tensor_map.h"
 
 namespace rt {
@@ -57,7 +58,7 @@ struct SlabArgs {
   uint32_t ns;        // slabs per chunk (c / X)
   uint32_t nch;       // chunks per block (R m)
   uint32_t slab;      // bytes per slab buffer (a multiple of 1024)
-  uint32_t box_bytes;  // 128 mb nr
+  uint32_t box_bytes;  // 4 X mb nr
   float c0, c1;
   uint32_t* status;
 };

@@ -85,7 +85,7 @@ cudaError_t launch_stencil2d_colring(const void* in, float* out, uint64_t nx, ui
                                      int sm_count, int max_smem, uint32_t* status,
                                      cudaStream_t st);
 
-// static(c) and dynamic(c) 2-D stencil, c a multiple of 32 dividing nx, team
+// static(c) and dynamic(c) 2-D stencil, c a multiple of 16 dividing nx, team
 // blocks of whole rows: each warp's chunks arrive slab by slab as swizzled
 // tensor copies (k_stencil_slabs.cu); cudaErrorNotSupported (nothing
 // launched) for other launches.
