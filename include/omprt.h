@@ -232,8 +232,8 @@ omprt_status omprt_set_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_team);
  * nx is a multiple of 4, n < 2^32, both pointers are 16-byte aligned,
  * thread_limit <= 512 and the ring holds one team's rows with room to spare;
  * other launches run the forms of omprt_set_stage_bytes.  bytes is rounded
- * down to 16; 0 turns this form off, and with it the slab, band, column-ring
- * and row-ring forms of omprt_set_stencil_slab_shape and the row ring of
+ * down to 16; 0 turns this form off, and with it the slab, band and column-ring
+ * forms of omprt_set_stencil_slab_shape and the row ring of
  * dynamic(c) (those size their buffers from the device's shared memory);
  * more than the device's per-block shared memory is OMPRT_ERR_INVALID.
  * Default after init: 226 KiB. */
