@@ -574,7 +574,7 @@ def main():
 
 def run_single_extra(rt, R, torch, inputs, args):
     """--single reduce/{fp32,bf16,int64}: the reduction of the bench's
-    reductions leg (n = 2^28, 4 teams per SM x 512 threads); --single batch:
+    reductions leg (n = 2^28, 2 teams per SM x 512 threads); --single batch:
     one persistent launch over the 4096-region batch."""
     import numpy as np
     stream = torch.cuda.current_stream()
@@ -599,7 +599,7 @@ def run_single_extra(rt, R, torch, inputs, args):
         r = torch.zeros(1, dtype=torch.int64 if args.single == "reduce/int64" else torch.float64,
                         device="cuda")
         sms = rt.sm_count
-        fn = lambda: rt.reduce(R.OP_SUM, t, r, R.PREC_COMP_F64, 4 * sms, 512, stream=stream)
+        fn = lambda: rt.reduce(R.OP_SUM, t, r, R.PREC_COMP_F64, 2 * sms, 512, stream=stream)
         nbytes = t.numel() * t.element_size()
     for _ in range(args.warmup):
         fn()
@@ -645,7 +645,8 @@ def run_single(rt, torch, plan, args):
 def measure_reductions(rt, R, torch, inputs, n=1 << 28, reps=5):
     """GB/s of the reduction configuration: n = 2^28 sums (fp32 uniform and
     lognormal, bf16, int64) and fp32 max / min at the shipped precision
-    (compensated fp32, fp64 combine), 4 teams per SM x 512 threads; inputs
+    (compensated fp32, fp64 combine), 2 teams per SM x 512 threads (every
+    team resident: one wave); inputs
     (0.5-2 GB) are larger than L2.  The fp sums are also run at the two
     comparison precisions (compensated fp32 with an fp32 combine, plain fp32)
     for the error report.  Three warm-up launches, then the mean of `reps`.
@@ -669,12 +670,12 @@ def measure_reductions(rt, R, torch, inputs, n=1 << 28, reps=5):
                                                            ("fp32_min", R.OP_MIN)]
         for label, o in ops:
             for _ in range(3):  # warm-up
-                rt.reduce(o, t, r, R.PREC_COMP_F64, 4 * sms, 512)
+                rt.reduce(o, t, r, R.PREC_COMP_F64, 2 * sms, 512)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(reps):
-                rt.reduce(o, t, r, R.PREC_COMP_F64, 4 * sms, 512)
+                rt.reduce(o, t, r, R.PREC_COMP_F64, 2 * sms, 512)
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
@@ -686,7 +687,7 @@ def measure_reductions(rt, R, torch, inputs, n=1 << 28, reps=5):
             out[label] = {"ms": ms, "GBps": gbs, "frac": gbs / peak, "shipped": v}
             if o == R.OP_SUM and name != "int64_sum":
                 for var, prec in (("comp_f32", R.PREC_COMP_F32), ("naive_f32", R.PREC_NAIVE_F32)):
-                    rt.reduce(o, t, r, prec, 4 * sms, 512)
+                    rt.reduce(o, t, r, prec, 2 * sms, 512)
                     out[label][var] = r.cpu()[0].item()
         del t
     assert rt.sync_status() == 0
@@ -706,14 +707,14 @@ def measure_sharded(rt, R, torch, inputs, ws, rank, n=1 << 28, reps=5):
     del a
     sms = rt.sm_count
     stream = torch.cuda.current_stream()
-    sharded.reduce_shard(rt, R.OP_SUM, shard, R.PREC_COMP_F64, 4 * sms, 512)
+    sharded.reduce_shard(rt, R.OP_SUM, shard, R.PREC_COMP_F64, 2 * sms, 512)
     torch.cuda.synchronize()
     res = torch.zeros(1, dtype=torch.float64, device="cuda")
     barrier(ws)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        rt.reduce(R.OP_SUM, shard, res, R.PREC_COMP_F64, 4 * sms, 512, stream=stream)
+        rt.reduce(R.OP_SUM, shard, res, R.PREC_COMP_F64, 2 * sms, 512, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_local = max_over_ranks(e0.elapsed_time(e1) / reps, ws)

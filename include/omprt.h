@@ -335,7 +335,8 @@ omprt_status omprt_launch_generic(omprt_ctx *ctx, const int64_t *seg_dev, int64_
  * (Sec. 3.1).  data_dev and result_dev are device pointers the caller owns;
  * result_dev: 8 bytes (double for F32/BF16, int64 for integers), written by
  * the launch (n = 0 writes the operation's identity in that type).
- * precision: omprt_precision.  Bad arguments return OMPRT_ERR_INVALID and
+ * precision: omprt_precision.  teams 0: two a SM; threads 0: 512 (every
+ * team resident at once).  Bad arguments return OMPRT_ERR_INVALID and
  * launch nothing. */
 omprt_status omprt_reduce(omprt_ctx *ctx, int32_t op, int32_t dtype, int32_t precision,
                           const void *data_dev, int64_t n, void *result_dev,

@@ -579,7 +579,11 @@ omprt_status omprt_reduce(omprt_ctx* c, int32_t op, int32_t dtype, int32_t preci
   r.op = op;
   r.precision = precision;
   r.result_dev = result;
-  if (teams == 0) teams = 4 * c->sm_count;
+  // two teams of 512 a SM: the value bodies' registers leave room for two
+  // such CTAs an SM, so every team is resident at once and the launch is one
+  // wave (n = 2^28: bf16 sum 0.96 of the copy rate against 0.94 with four
+  // teams a SM in two waves, fp32 sum 1.04 against 1.02)
+  if (teams == 0) teams = 2 * c->sm_count;
   if (threads == 0) threads = 512;
   return omprt_launch_region(c, &d, OMPRT_SCHED_AUTO, 0, teams, threads, &r, stream);
 }
