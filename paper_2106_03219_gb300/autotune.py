@@ -3,7 +3,7 @@
 The worksharing sweep times each (body, schedule) over the grid
 teams x threads and records the fastest point; the table is what the
 benchmark and the batched executor use.  The team counts include powers of
-two besides multiples of the SM count: with n a power of two they make every
+two besides multiples of the SM count (`team_grid`): with n a power of two they make every
 team's block start on a 32-byte boundary, so per-thread chunks are whole
 vectors.  Timing: CUDA events on the launching stream around launches that
 go back to back over four copies of the buffers in turn (each launch's
@@ -18,7 +18,15 @@ import statistics
 PKG = os.path.dirname(os.path.abspath(__file__))
 SWEEP_TABLE = os.path.join(PKG, "tuned", "sweep_gb300.json")
 
-TEAMS = (148, 296, 592, 1024, 1184, 2048, 2368, 4096, 8192, 16384)
+# team counts: powers of two, and multiples of the device's SM count (see
+# team_grid), where every SM gets the same number of teams
+TEAMS_POW2 = (1024, 2048, 4096, 8192, 16384)
+SM_MULTIPLES = (1, 2, 4, 8, 16, 32)
+
+
+def team_grid(sm_count):
+    """The sweep's team counts on a device of sm_count SMs."""
+    return tuple(sorted(set(TEAMS_POW2) | {m * sm_count for m in SM_MULTIPLES}))
 THREADS = (32, 64, 128, 256, 512, 1024)
 SCHEDULES = [("static1", 1, 1), ("static8", 1, 8), ("static64", 1, 64), ("static", 0, 0),
              ("dynamic256", 2, 256), ("auto", 3, 0)]
@@ -76,7 +84,7 @@ def load_sweep_table(path=SWEEP_TABLE):
     return json.load(open(path)).get("best")
 
 
-def sweep(rt, n_axpy=1 << 26, grid=4096, reps=3, teams=TEAMS, threads=THREADS, log=None,
+def sweep(rt, n_axpy=1 << 26, grid=4096, reps=3, teams=None, threads=THREADS, log=None,
           nsets=4):
     """The worksharing sweep: axpy (12 B/iter) and 2-D stencil (8 B/point)
     under every schedule at every (teams, threads).  Returns (rows, best)."""
@@ -84,6 +92,8 @@ def sweep(rt, n_axpy=1 << 26, grid=4096, reps=3, teams=TEAMS, threads=THREADS, l
     from . import inputs
     from . import omprt as R
 
+    if teams is None:
+        teams = team_grid(rt.sm_count)
     sets = []
     for _ in range(nsets):
         x = torch.from_numpy(inputs.f32_uniform01(n_axpy, 0)).cuda()

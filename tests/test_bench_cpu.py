@@ -31,3 +31,14 @@ def test_reference_arm_json_line():
     assert one["cores"] == 1 and one["value"] > 0
     assert "workload" in d["config"] and "4096x4096" in d["config"]["workload"]
 
+
+
+def test_sweep_team_grid_follows_the_sm_count():
+    from paper_2106_03219_gb300 import autotune
+    g = autotune.team_grid(152)
+    assert list(g) == sorted(set(g))
+    for m in (1, 2, 4, 8, 16, 32):
+        assert 152 * m in g
+    for p in (1024, 2048, 4096, 8192, 16384):
+        assert p in g
+    assert 148 not in g and 1184 not in g
