@@ -781,7 +781,8 @@ def measure_kernels_steady(rt, R, torch, launches, plan, peak, nsets=4, reps=3):
     own kind.  In the step itself a stencil launch follows an 805 MB axpy and
     pays for the write-back of that axpy's dirty lines (up to L2's size),
     and the axpy after it pays less; these figures take that cross-charge
-    out."""
+    out.  `device_copy_of_the_grid` times a plain device copy of the
+    stencil's 134 MB the same way: the ceiling at that launch size."""
     from paper_2106_03219_gb300 import inputs
     sets = []
     for k in range(nsets):
@@ -809,6 +810,22 @@ def measure_kernels_steady(rt, R, torch, launches, plan, peak, nsets=4, reps=3):
         gbs = nbytes / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "GBps": gbs, "frac": gbs / peak}
     assert rt.sync_status() == 0
+    # the same-size ceiling: a plain device copy (torch's) of the stencil's
+    # bytes, the grid in and out, launched the same way over the same buffers
+    for (xx, yy, gg, oo), _ in sets:
+        oo.copy_(gg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        for (xx, yy, gg, oo), _ in sets:
+            oo.copy_(gg)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (reps * nsets)
+    gbs = 8 * GRID * GRID / (ms * 1e-3) / 1e9
+    out["device_copy_of_the_grid"] = {"ms": ms, "GBps": gbs, "frac": gbs / peak,
+                                      "kernel": "torch copy_ (library), not in the step"}
     del sets
     return out
 
