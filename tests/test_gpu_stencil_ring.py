@@ -108,3 +108,31 @@ def test_stencil_stage_bytes_validation(rt):
     with pytest.raises(R.OmprtError):
         rt.set_stencil_stage_bytes(1 << 30)
     rt.set_stencil_stage_bytes(DEFAULT_BUDGET)
+
+
+@pytest.mark.parametrize("stage", [32768, 0])
+def test_every_schedule_without_the_stencil_budget(ring, stage):
+    """With the stencil stage budget at 0 the ring, slab, band and column forms
+    are off: every schedule takes the strips, the row passes or (with the
+    staged-region budget also 0) the plain region kernel, bit-exact."""
+    import torch
+    rt = ring
+    rt.set_stencil_stage_bytes(0)
+    rt.set_stage_bytes(stage)
+    try:
+        for ny, nx in ((40, 512), (33, 4096), (7, 100)):
+            a = inputs.grid_f32(ny, nx, 19)
+            ad = dev(a)
+            want = bits32(O.stencil2d5(a))
+            for sched, chunk in ((R.SCHED_STATIC, 0), (R.SCHED_STATIC_CHUNKED, 1),
+                                 (R.SCHED_STATIC_CHUNKED, 8), (R.SCHED_STATIC_CHUNKED, 64),
+                                 (R.SCHED_DYNAMIC, 64), (R.SCHED_DYNAMIC, 256),
+                                 (R.SCHED_AUTO, 0)):
+                for G, T in ((ny, 32), (ny, 64), (1, 512), (5, 128)):
+                    out = torch.full((ny, nx), -7.0, device="cuda")
+                    rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=ny * nx, x=ad, out=out,
+                                                 nx=nx, ny=ny), sched, chunk, G, T)
+                    assert np.array_equal(bits32(host(out)), want), (ny, nx, sched, chunk, G, T)
+    finally:
+        rt.set_stage_bytes(32768)
+    assert rt.sync_status() == 0
