@@ -7,7 +7,11 @@ static(1), static(8), static(64), static (no chunk), dynamic(256) and auto,
 at the teams / threads the tuning table gives for that schedule.
 
 value     = algorithmic bytes of the step (12 B per axpy iteration, 8 B per
-            stencil point) / device time of the step (CUDA events).
+            stencil point) / device time of the step (CUDA events), the
+            launches back to back on one stream, each free to start under the
+            previous one's tail (launch overlap, the runtime's default); an
+            event pair brackets the dominant kernel only.
+launch_overlap = the same step with plain launches.
 e2e       = the same bytes / time of a step through the C ABI with the inputs
             copied in from pinned host memory and the results copied back.
 roofline  = the kernel with the largest share of the step: its algorithmic
@@ -15,8 +19,11 @@ roofline  = the kernel with the largest share of the step: its algorithmic
             copy bandwidth.
 cpu_baseline / --impl reference = the CPU oracle on the same workload, on all
             host cores (one slice per core) and on one core.
-kernels   = per-kernel event times inside the timed step; kernels_steady =
-            each kernel alone, back to back over rotating buffer copies.
+kernels   = per-kernel event times in a pass of the step with every launch
+            between its own event pair (serialised, about 1.5 us of event
+            cost each); kernels_steady = each kernel alone, back to back over
+            rotating buffer copies, with launch overlap and (plain_launches)
+            without.
 
 Launch: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference];
 for N > 1 under torch.distributed.run, every rank runs the same workload on
@@ -471,48 +478,74 @@ def main():
         return run_single(rt, torch, plan, args)
     step_bytes = sum(b for _, b, *_ in plan)
 
-    def run_step(record=None):
+    def new_events():
+        return (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def run_step(record=None, only=None):
+        """One step; record[i] brackets launch i with events (all launches, or
+        launch `only` alone)."""
         for i, (name, _, desc, sched, chunk, G, T) in enumerate(plan):
-            if record is not None:
-                record[i][0].record(stream)
+            mark = record is not None and (only is None or i == only)
+            if mark:
+                record[i if only is None else 0][0].record(stream)
             rt.launch_region(desc, sched, chunk, G, T, stream=stream)
-            if record is not None:
-                record[i][1].record(stream)
+            if mark:
+                record[i if only is None else 0][1].record(stream)
 
     for _ in range(args.warmup):
         run_step()
     torch.cuda.synchronize()
     assert rt.sync_status() == 0
 
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in plan] for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
-    barrier(ws)
-    torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
+    # Per-kernel breakdown, outside the timed region: each launch between its
+    # own event pair.  An event between two launches orders them (the second
+    # no longer overlaps the first one's tail) and costs about 1.5 us itself,
+    # so these times include that and the step below carries events around
+    # its dominant kernel only.
+    evk = [[new_events() for _ in plan] for _ in range(args.steps)]
     for k in range(args.steps):
-        run_step(ev[k])
-    t_end.record(stream)
+        run_step(evk[k])
     torch.cuda.synchronize()
-    barrier(ws)
-    clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
-    ms_total = max_over_ranks(ms_total, ws)
-    ms_step = ms_total / args.steps
-    value = step_bytes * ws / (ms_step * 1e-3) / 1e9
-    assert rt.sync_status() == 0
-
-    # per-kernel mean launch times; the dominant kernel is the largest share
     per = {}
     for i, (name, nbytes, *_rest) in enumerate(plan):
-        ts = [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)]
+        ts = [evk[k][i][0].elapsed_time(evk[k][i][1]) for k in range(args.steps)]
         per[name] = (nbytes, statistics.mean(ts))
     dom = max(per, key=lambda k: per[k][1])
+    dom_i = [p[0] for p in plan].index(dom)
+
+    def timed_steps(ev):
+        barrier(ws)
+        torch.cuda.synchronize()
+        t_start, t_end = new_events()
+        t_start.record(stream)
+        for k in range(args.steps):
+            run_step(ev[k], only=dom_i)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        return max_over_ranks(t_start.elapsed_time(t_end), ws) / args.steps
+
+    ev = [[new_events()] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_step = timed_steps(ev)
+    clk = clocks.stop()
+    value = step_bytes * ws / (ms_step * 1e-3) / 1e9
+    assert rt.sync_status() == 0
+    dom_ms = statistics.mean(ev[k][0][0].elapsed_time(ev[k][0][1]) for k in range(args.steps))
+
+    # the same step with plain launches (no overlap of a launch with the
+    # previous one's tail), for comparison; not the reported value
+    rt.set_launch_overlap(False)
+    ev_off = [[new_events()] for _ in range(args.steps)]
+    ms_step_off = timed_steps(ev_off)
+    rt.set_launch_overlap(True)
+    assert rt.sync_status() == 0
+    overlap_line = {"ms_per_step_plain_launches": ms_step_off,
+                    "value_plain_launches": step_bytes * ws / (ms_step_off * 1e-3) / 1e9}
+
     peak, peak_kind = measured_peaks()
-    achieved = per[dom][0] / (per[dom][1] * 1e-3) / 1e9
+    achieved = per[dom][0] / (dom_ms * 1e-3) / 1e9
     traffic = traffic_for(dom)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": dom,
@@ -560,6 +593,7 @@ def main():
                 "dtype": "f32", "data": "synthetic", "config": config_dict(points),
                 "e2e": e2e_line, "roofline": roofline, "cpu_baseline": cpu,
                 "gpu_launches": len(plan) * args.steps, "clocks": clk,
+                "launch_overlap": overlap_line,
                 "kernels": kernels, "kernels_steady": steady, "single_region": single,
                 "sharded_reduction": sharded_red,
                 "reductions": reductions, "batched": batched_forms, "learned": learned_eval,
@@ -781,8 +815,10 @@ def measure_kernels_steady(rt, R, torch, launches, plan, peak, nsets=4, reps=3):
     own kind.  In the step itself a stencil launch follows an 805 MB axpy and
     pays for the write-back of that axpy's dirty lines (up to L2's size),
     and the axpy after it pays less; these figures take that cross-charge
-    out.  `device_copy_of_the_grid` times a plain device copy of the
-    stencil's 134 MB the same way: the ceiling at that launch size."""
+    out.  Launches overlap the previous one's tail (the runtime's default);
+    `plain_launches` repeats the figures without that.
+    `device_copy_of_the_grid` times a plain device copy of the stencil's
+    134 MB the same way: the ceiling at that launch size for plain launches."""
     from paper_2106_03219_gb300 import inputs
     sets = []
     for k in range(nsets):
@@ -792,8 +828,8 @@ def measure_kernels_steady(rt, R, torch, launches, plan, peak, nsets=4, reps=3):
         oo = torch.empty_like(gg)
         sets.append(((xx, yy, gg, oo), launches(xx, yy, gg, oo)))
     stream = torch.cuda.current_stream()
-    out = {}
-    for i, (name, nbytes, *_r) in enumerate(plan):
+
+    def alone(i):
         for _, L in sets:
             _, _, d, sched, chunk, G, T = L[i]
             rt.launch_region(d, sched, chunk, G, T, stream=stream)
@@ -806,9 +842,19 @@ def measure_kernels_steady(rt, R, torch, launches, plan, peak, nsets=4, reps=3):
                 rt.launch_region(d, sched, chunk, G, T, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / (reps * nsets)
+        return e0.elapsed_time(e1) / (reps * nsets)
+
+    out, plain = {}, {}
+    for i, (name, nbytes, *_r) in enumerate(plan):
+        ms = alone(i)
         gbs = nbytes / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "GBps": gbs, "frac": gbs / peak}
+    rt.set_launch_overlap(False)
+    for i, (name, nbytes, *_r) in enumerate(plan):
+        ms = alone(i)
+        plain[name] = {"ms": ms, "frac": nbytes / (ms * 1e-3) / 1e9 / peak}
+    rt.set_launch_overlap(True)
+    out["plain_launches"] = plain
     assert rt.sync_status() == 0
     # the same-size ceiling: a plain device copy (torch's) of the stencil's
     # bytes, the grid in and out, launched the same way over the same buffers
@@ -825,7 +871,8 @@ def measure_kernels_steady(rt, R, torch, launches, plan, peak, nsets=4, reps=3):
     ms = e0.elapsed_time(e1) / (reps * nsets)
     gbs = 8 * GRID * GRID / (ms * 1e-3) / 1e9
     out["device_copy_of_the_grid"] = {"ms": ms, "GBps": gbs, "frac": gbs / peak,
-                                      "kernel": "torch copy_ (library), not in the step"}
+                                      "kernel": "torch copy_ (library, plain launches), "
+                                                "not in the step"}
     del sets
     return out
 

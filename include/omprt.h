@@ -255,6 +255,23 @@ omprt_status omprt_set_stencil_stage_bytes(omprt_ctx *ctx, int64_t bytes_per_cta
  * ring: 3).  Other values: OMPRT_ERR_INVALID, nothing changed. */
 omprt_status omprt_set_stencil_slab_shape(omprt_ctx *ctx, int32_t slab_floats, int32_t buffers);
 
+/* Whether the regions this context launches may overlap the tail of the
+ * previous kernel on their stream.  On (non-zero, the default after init),
+ * every executor kernel is launched with programmatic stream serialisation:
+ * its blocks may be scheduled while the kernel before it on the stream
+ * drains, and each block waits, before its first global memory access, until
+ * that kernel has completed and its writes are visible, so results and
+ * stream order are the same as with plain launches.  A region launched right
+ * after another on the same stream then starts without the launch gap (a
+ * 4096 x 4096 copy-sized launch saves about 2.4 us).  A launch asking for at
+ * least 16 KiB less dynamic shared memory than the previous one on its stream
+ * (made by this library on the same host thread), where blocks of both fit
+ * one SM, is made plain: blocks started early beside the previous grid's
+ * would run with that grid's small L1.  An event recorded between two
+ * launches orders them as before.  omprt_reduce_noalloc, which takes no
+ * context, always launches this way.  Off (0): plain launches. */
+omprt_status omprt_set_launch_overlap(omprt_ctx *ctx, int32_t on);
+
 /*
  * Run one "target teams distribute parallel for" region:
  *   level 1: the n logical iterations are split among num_teams teams in

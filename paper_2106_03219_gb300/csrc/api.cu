@@ -182,6 +182,7 @@ omprt_status omprt_init(int device, omprt_ctx** out) {
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, device);
   cudaDeviceGetAttribute(&c->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
   c->stack_bytes = 4096;
   c->stencil_stage_bytes = kStencilStageDefault;
   bool ok = cudaMalloc(&c->status_dev, 256) == cudaSuccess &&
@@ -241,6 +242,12 @@ omprt_status omprt_set_stencil_slab_shape(omprt_ctx* c, int32_t slab_floats, int
     return OMPRT_ERR_INVALID;
   c->slab_floats = (uint32_t)slab_floats;
   c->slab_buffers = (uint32_t)buffers;
+  return OMPRT_OK;
+}
+
+omprt_status omprt_set_launch_overlap(omprt_ctx* c, int32_t on) {
+  if (!c) return OMPRT_ERR_NOT_INIT;
+  c->launch_overlap = on != 0;
   return OMPRT_OK;
 }
 
@@ -392,6 +399,7 @@ static omprt_status launch_region_impl(omprt_ctx* c, const omprt_loop_desc* d, i
   if ((acc != kAccNone || counters) && teams > OMPRT_MAX_RED_TEAMS) return OMPRT_ERR_INVALID;
 
   DeviceGuard guard(c->device);
+  rt::OverlapScope overlap(c->launch_overlap, (size_t)c->smem_per_sm);
   RegionArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = n;

@@ -12,6 +12,7 @@ struct omprt_ctx {
   int sm_count = 0;
   int l2_bytes = 0;
   int max_smem_optin = 0;
+  int smem_per_sm = 0;
   uint32_t* status_dev = nullptr;
   unsigned char* slots_dev = nullptr;
   unsigned char* pool_dev = nullptr;
@@ -21,6 +22,7 @@ struct omprt_ctx {
   uint32_t stencil_stage_bytes = 0;  // per-CTA shared memory for the staged 2-D stencil windows
   uint32_t slab_floats = 0;   // 2-D stencil slabs: floats a line (16 / 32; 0 the default)
   uint32_t slab_buffers = 0;  // and buffers a warp (2 .. 4; 0 the default)
+  bool launch_overlap = true;  // executor launches overlap the previous grid's tail
   std::atomic<uint32_t> next_slot{0};
   // learned schedule (host copy of the model)
   bool has_model = false;

@@ -81,6 +81,7 @@ __device__ __forceinline__ RegionArgs region_args(const BatchRegion& R) {
 }
 
 __global__ void __launch_bounds__(1024) batch_kernel(const BatchArgs A) {
+  enter_region_grid();
   __shared__ unsigned long long s_item;
   __shared__ int s_last;
   __shared__ double s_scr[32];
@@ -257,6 +258,7 @@ omprt_status omprt_launch_batch(omprt_batch* b, int32_t num_ctas, int32_t thread
   if (threads == 0) threads = 256;
   if (threads < 64 || threads > 1024 || threads % 32 || num_ctas < 0) return OMPRT_ERR_INVALID;
   DeviceGuard guard(b->ctx->device);
+  OverlapScope overlap(b->ctx->launch_overlap, (size_t)b->ctx->smem_per_sm);
   if (num_ctas == 0) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, threads, 0) !=
@@ -275,8 +277,8 @@ omprt_status omprt_launch_batch(omprt_batch* b, int32_t num_ctas, int32_t thread
   a.head = b->head_dev;
   a.exits = (uint32_t*)(b->head_dev + 1);
   a.status = b->ctx->status_dev;
-  batch_kernel<<<num_ctas, threads, 0, (cudaStream_t)stream>>>(a);
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e =
+      launch_kernel(batch_kernel, dim3(num_ctas), dim3(threads), 0, (cudaStream_t)stream, a);
   return e == cudaSuccess ? OMPRT_OK : OMPRT_ERR_CUDA;
 }
 

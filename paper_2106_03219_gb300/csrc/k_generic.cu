@@ -100,6 +100,7 @@ __device__ __forceinline__ float2 generic_for(const Body& body, uint64_t lo, uin
 }
 
 __global__ void __launch_bounds__(1024) generic_kernel(const GenericArgs A) {
+  enter_region_grid();
   __shared__ WorkDesc s_work;  // the team-shared hand-over word
   const uint32_t t = threadIdx.x, g = blockIdx.x, G = gridDim.x;
   if (t == 0)
@@ -221,6 +222,7 @@ extern "C" omprt_status omprt_launch_generic(omprt_ctx* c, const int64_t* seg_de
   if (teams < 1) return OMPRT_ERR_INVALID;
   if (nseg == 0) return OMPRT_OK;
   DeviceGuard guard(c->device);
+  OverlapScope overlap(c->launch_overlap, (size_t)c->smem_per_sm);
   GenericArgs a;
   a.seg = seg_dev;
   a.nseg = (uint64_t)nseg;
@@ -241,6 +243,8 @@ extern "C" omprt_status omprt_launch_generic(omprt_ctx* c, const int64_t* seg_de
     cudaGetLastError();
     return OMPRT_ERR_CUDA;
   }
-  generic_kernel<<<teams, threads, a.stack_bytes, (cudaStream_t)stream>>>(a);
-  return cudaGetLastError() == cudaSuccess ? OMPRT_OK : OMPRT_ERR_CUDA;
+  return launch_kernel(generic_kernel, dim3(teams), dim3(threads), a.stack_bytes,
+                       (cudaStream_t)stream, a) == cudaSuccess
+             ? OMPRT_OK
+             : OMPRT_ERR_CUDA;
 }

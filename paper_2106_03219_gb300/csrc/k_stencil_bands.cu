@@ -61,6 +61,7 @@ __device__ __forceinline__ float lds32_at(uint32_t addr) {
 template <int M>
 __global__ void __launch_bounds__(1024) stencil2d_bands_kernel(
     const __grid_constant__ CUtensorMap map, const BandArgs A) {
+  enter_region_grid();
   __shared__ __align__(8) uint64_t bars[32][kBandMaxNB];
   const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5, T = blockDim.x;
   const uint32_t NB = A.NB, Rb = A.Rb;
@@ -215,8 +216,7 @@ cudaError_t launch_stencil2d_bands(const void* in, float* out, uint64_t nx, uint
   if (per_sm < 1) return cudaErrorNotSupported;
   uint64_t P = (uint64_t)per_sm * (uint64_t)sm_count;
   if (P > teams) P = teams;
-  kern<<<(unsigned)P, threads, smem, st>>>(map, a);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3((unsigned)P), dim3(threads), smem, st, map, a);
 }
 
 }  // namespace rt

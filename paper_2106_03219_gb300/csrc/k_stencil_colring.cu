@@ -52,6 +52,7 @@ struct ColArgs {
 template <int SCHED>
 __global__ void __launch_bounds__(1024) stencil2d_colring_kernel(
     const __grid_constant__ CUtensorMap map, const ColArgs A) {
+  enter_region_grid();
   __shared__ __align__(8) uint64_t full[kColMaxNB], empty[kColMaxNB];
   __shared__ uint32_t ctr[SCHED == kDynamic ? kColMaxTeams : 1];  // the teams' claim counters
   __shared__ int s_bad;
@@ -261,8 +262,7 @@ cudaError_t launch_stencil2d_colring(const void* in, float* out, uint64_t nx, ui
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)(32 * K + 32), smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorNotSupported;
-  kern<<<(unsigned)P, (unsigned)(32 * K + 32), smem, st>>>(map, a);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3((unsigned)P), dim3((unsigned)(32 * K + 32)), smem, st, map, a);
 }
 
 }  // namespace rt

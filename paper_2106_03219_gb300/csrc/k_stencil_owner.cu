@@ -247,6 +247,7 @@ __device__ __forceinline__ void owner_piece(const OwnerArgs& A, const Win& W, ui
 
 template <int SCHED>
 __global__ void __launch_bounds__(1024) stencil2d_owner_kernel(const OwnerArgs A) {
+  enter_region_grid();
   __shared__ __align__(8) uint64_t full[kOwnerMaxSlots], empty[kOwnerMaxSlots];
   __shared__ uint32_t ctr[kOwnerMaxGroups][2];  // dynamic: each group's claim counters
   __shared__ int s_bad;
@@ -470,8 +471,7 @@ cudaError_t launch_stencil2d_owner(const void* in, float* out, uint64_t nx, uint
   const uint64_t per_cta = a.G / P;  // every CTA has at least this many teams
   if (K > per_cta) K = per_cta;
   a.groups = (uint32_t)K;
-  kern<<<(unsigned)P, (unsigned)(K * threads + 32), smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3((unsigned)P), dim3((unsigned)(K * threads + 32)), smem, st, a);
 }
 
 }  // namespace rt

@@ -163,6 +163,7 @@ __device__ __forceinline__ void rr_chunk(const RowRingArgs& A, const float* ring
 }
 
 __global__ void __launch_bounds__(1024) stencil2d_rowring_kernel(const RowRingArgs A) {
+  enter_region_grid();
   __shared__ __align__(8) uint64_t full[kRrMaxSlots], empty[kRrMaxSlots];
   __shared__ uint32_t ctr[kRrMaxGroups][2];  // dynamic: each group's claim counters
   __shared__ int s_bad;
@@ -355,8 +356,7 @@ cudaError_t launch_stencil2d_rowring(const void* in, float* out, uint64_t nx, ui
   const uint64_t per_cta = teams / P;  // every CTA has at least this many teams
   if (K > per_cta) K = per_cta;
   a.K = (uint32_t)K;
-  kern<<<(unsigned)P, (unsigned)(K * threads + 32), smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3((unsigned)P), dim3((unsigned)(K * threads + 32)), smem, st, a);
 }
 
 }  // namespace rt

@@ -87,6 +87,7 @@ __device__ __forceinline__ void rows_unit(const RowsArgs& A, const float* ring, 
 }
 
 __global__ void __launch_bounds__(1024) stencil2d_rows_kernel(const RowsArgs A) {
+  enter_region_grid();
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_bad;
   float* const ring = (float*)rt_dyn_smem;  // 2K + 2 slots of slot_floats
@@ -214,8 +215,7 @@ cudaError_t launch_stencil2d_rows(const void* in, float* out, uint64_t nx, uint6
   static const size_t static_bytes = static_smem_of(stencil2d_rows_kernel);
   const cudaError_t e = smem_optin(stencil2d_rows_kernel, smem, static_bytes);
   if (e != cudaSuccess) return e;
-  stencil2d_rows_kernel<<<teams, threads, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(stencil2d_rows_kernel, dim3(teams), dim3(threads), smem, st, a);
 }
 
 }  // namespace rt

@@ -75,6 +75,7 @@ struct SlabItem {
 template <int SCHED, int X, int NB>
 __global__ void __launch_bounds__(kSlabMaxWarps * 32, 1) stencil2d_slabs_kernel(
     const __grid_constant__ CUtensorMap map, const SlabArgs A) {
+  enter_region_grid();
   constexpr uint32_t U = X / 4;  // 16-byte units of a line
   __shared__ __align__(8) uint64_t bars[kSlabMaxWarps][NB];
   __shared__ uint32_t ctr[SCHED == kDynamic ? kSlabMaxTeams : 1];  // the teams' claim counters
@@ -356,8 +357,7 @@ cudaError_t launch_stencil2d_slabs(const void* in, float* out, uint64_t nx, uint
   if (K > per_cta_max) K = per_cta_max;
   if (sched == kDynamic && per_cta_max > kSlabMaxTeams) return cudaErrorNotSupported;
   a.K = (uint32_t)K;
-  kern<<<(unsigned)P, (unsigned)(K * threads), smem, st>>>(map, a);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3((unsigned)P), dim3((unsigned)(K * threads)), smem, st, map, a);
 }
 
 }  // namespace rt

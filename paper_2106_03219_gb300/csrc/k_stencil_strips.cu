@@ -77,6 +77,7 @@ __device__ __forceinline__ void strip_store(float* p, const float (&v)[W]) {
 // r + 1 + D are in flight while row r computes).
 template <int W, int M, int D>
 __global__ void __launch_bounds__(1024) stencil2d_strips_kernel(const StripArgs A) {
+  enter_region_grid();
   const uint32_t t = threadIdx.x, T = blockDim.x, lane = t & 31u;
   const uint32_t P = gridDim.x, k = blockIdx.x;
   const uint32_t nx = A.nx, ny = A.ny;
@@ -191,8 +192,7 @@ cudaError_t launch_stencil2d_strips(const void* in, float* out, uint64_t nx, uin
   if (per_sm < 1) return cudaErrorNotSupported;
   uint64_t P = (uint64_t)per_sm * (uint64_t)sm_count;
   if (P > teams) P = teams;
-  kern<<<(unsigned)P, threads, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3((unsigned)P), dim3(threads), 0, st, a);
 }
 
 }  // namespace rt

@@ -63,6 +63,7 @@ __device__ __forceinline__ float stencil_point(float c0, float c1, float nn, flo
 template <int W>
 __global__ void __launch_bounds__(256) stencil2d_tiles_kernel(const __grid_constant__ CUtensorMap map,
                                                               const TileArgs A) {
+  enter_region_grid();
   constexpr uint32_t R = kTileY / W;
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_bad;
@@ -205,8 +206,7 @@ cudaError_t launch_stencil2d_tiles(const void* in, float* out, uint64_t nx, uint
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, 32 * warps, kTileSmem, st>>>(map, a);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3(grid), dim3(32 * warps), kTileSmem, st, map, a);
 }
 
 }  // namespace rt

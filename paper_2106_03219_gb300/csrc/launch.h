@@ -1,6 +1,8 @@
 // Host-side entry points of the executor translation units (internal).
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 
 #include "region.cuh"
@@ -23,6 +25,86 @@ template <class K>
 inline cudaError_t smem_optin(K kern, size_t dyn, size_t static_bytes) {
   if (dyn + static_bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
+// Launch overlap, per host thread: whether executor launches may overlap
+// the tail of the previous grid on their stream (programmatic stream
+// serialisation; on by default), the shared memory of one SM (0: unknown),
+// and the stream and dynamic shared memory of the last executor launch.  An
+// API call on a context sets the first two from the context for its duration
+// (OverlapScope).
+struct OverlapState {
+  bool on = true;
+  size_t smem_per_sm = 0;
+  cudaStream_t last_stream = nullptr;
+  size_t last_smem = 0;
+  bool any = false;
+};
+inline OverlapState& overlap_state() {
+  thread_local OverlapState s;
+  return s;
+}
+struct OverlapScope {
+  bool prev_on;
+  size_t prev_per_sm;
+  OverlapScope(bool on, size_t smem_per_sm) {
+    OverlapState& s = overlap_state();
+    prev_on = s.on;
+    prev_per_sm = s.smem_per_sm;
+    s.on = on;
+    s.smem_per_sm = smem_per_sm;
+  }
+  ~OverlapScope() {
+    overlap_state().on = prev_on;
+    overlap_state().smem_per_sm = prev_per_sm;
+  }
+  OverlapScope(const OverlapScope&) = delete;
+  OverlapScope& operator=(const OverlapScope&) = delete;
+};
+
+// A grid scheduled early lands beside the previous grid's blocks, and an SM
+// that keeps running blocks keeps the split of its on-chip memory between L1
+// and shared memory that the previous grid set.  A grid asking for much less
+// shared memory than the one before it (a streaming loop after a staged
+// stencil) would then run all its blocks with the small L1 of that split:
+// measured on GB300, an axpy of 2^26 floats after a 200 KB-a-block copy lost
+// 15 us that way, against 3 us gained by the overlap.  Such a launch is made
+// plain, so the SMs drain and take the new split; where the two grids cannot
+// share an SM, or ask for about the same, the launch overlaps.
+constexpr size_t kOverlapSmemStep = 16 * 1024;
+inline bool overlap_this_launch(cudaStream_t st, size_t smem) {
+  const OverlapState& s = overlap_state();
+  if (!s.on) return false;
+  if (!s.any || s.last_stream != st) return true;
+  const bool can_share = s.smem_per_sm == 0 || s.last_smem + smem <= s.smem_per_sm;
+  return !(can_share && s.last_smem >= smem + kOverlapSmemStep);
+}
+
+// Launch an executor kernel (one that starts with enter_region_grid).  The
+// launch error, if any, is returned and cleared.
+template <class... KArgs, class... Args>
+inline cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap_this_launch(st, smem) ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  OverlapState& s = overlap_state();
+  s.last_stream = st;
+  s.last_smem = smem;
+  s.any = true;
+  return e;
 }
 
 // Reduction accumulator selected for a launch.

@@ -12,8 +12,7 @@ inline cudaError_t launch_one(unsigned grid, unsigned block, size_t smem, cudaSt
   static const size_t static_bytes = static_smem_of(k);
   const cudaError_t e = smem_optin(k, smem, static_bytes);
   if (e != cudaSuccess) return e;
-  k<<<grid, block, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(k, grid, block, smem, st, a);
 }
 
 template <class Body, class Acc>

@@ -1212,6 +1212,7 @@ __device__ void run_staged(const Body& b, const RegionArgs& a, uint64_t bs, uint
 // ---------------------------------------------------------------------------
 template <class Body, int SCHED, class Acc>
 __global__ void __launch_bounds__(OMPRT_MAX_THREADS) region_kernel(const RegionArgs a) {
+  enter_region_grid();
   const uint32_t g = blockIdx.x, G = gridDim.x, t = threadIdx.x, T = blockDim.x;
   Body body(a);
   Acc acc;

@@ -25,6 +25,29 @@ __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ uint32_t warp_id() { return threadIdx.x >> 5; }
 
 // ---------------------------------------------------------------------------
+// Back-to-back regions on one stream (programmatic dependent launch, sm_90
+// and later).  The host launches every executor grid with programmatic
+// stream serialisation, so a grid may be scheduled while the grid before it
+// drains.  Each executor kernel therefore starts with `wait_for_prior_grid`,
+// before its first global load or store: it returns once the grid before it
+// has completed and that grid's writes are visible (at once when the grid was
+// launched without the attribute).  `allow_next_grid` then lets the next
+// grid start as soon as every block of this one is running; its blocks sit in
+// their own wait until this grid ends, so they only take over what this
+// grid's finished blocks leave free.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void wait_for_prior_grid() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_next_grid() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void enter_region_grid() {
+  wait_for_prior_grid();
+  allow_next_grid();
+}
+
+// ---------------------------------------------------------------------------
 // The five runtime atomics (Sec. 3.1, Listing 3 and the inc definition after
 // it), sequentially consistent on 32-bit words at device scope: a full fence
 // on both sides of the hardware read-modify-write.

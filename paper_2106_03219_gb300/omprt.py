@@ -70,6 +70,7 @@ def _declare(L):
         "omprt_set_stage_bytes": (st, [vp, i64]),
         "omprt_set_stencil_stage_bytes": (st, [vp, i64]),
         "omprt_set_stencil_slab_shape": (st, [vp, i32, i32]),
+        "omprt_set_launch_overlap": (st, [vp, i32]),
         "omprt_launch_region": (st, [vp, C.POINTER(LoopDesc), i32, i64, i32, i32,
                                      C.POINTER(ReduceDesc), vp]),
         "omprt_launch_region_dist": (st, [vp, C.POINTER(LoopDesc), i64, i32, i64, i32, i32,
@@ -222,6 +223,12 @@ class Runtime:
         warp (2 .. 4) of the 2-D stencil's slab form; 0 the default."""
         check(lib().omprt_set_stencil_slab_shape(self.ctx, int(slab_floats), int(buffers)),
               "omprt_set_stencil_slab_shape")
+
+    def set_launch_overlap(self, on=True):
+        """omprt_set_launch_overlap: launch regions so that each may start while
+        the kernel before it on the stream drains (True, the default) or as
+        plain launches (False)."""
+        check(lib().omprt_set_launch_overlap(self.ctx, 1 if on else 0), "omprt_set_launch_overlap")
 
     def set_stencil_stage_bytes(self, nbytes):
         """omprt_set_stencil_stage_bytes: per-CTA shared memory for the staged 2-D

@@ -52,6 +52,7 @@ def test_null_context_is_rejected(L):
     assert L.omprt_set_stage_bytes(None, 16) == R.ERR_NOT_INIT
     assert L.omprt_set_stencil_stage_bytes(None, 16) == R.ERR_NOT_INIT
     assert L.omprt_set_stencil_slab_shape(None, 0, 0) == R.ERR_NOT_INIT
+    assert L.omprt_set_launch_overlap(None, 1) == R.ERR_NOT_INIT
     assert L.omprt_launch_generic(None, None, 0, C.byref(d), 0, None, 0, 0, None) == \
         R.ERR_NOT_INIT
     assert L.omprt_finalize(None) == R.ERR_NOT_INIT
