@@ -23,12 +23,22 @@ pytestmark = pytest.mark.gpu
 ST, CH, DY, AU, GU = (R.SCHED_STATIC, R.SCHED_STATIC_CHUNKED, R.SCHED_DYNAMIC, R.SCHED_AUTO,
                       R.SCHED_GUIDED)
 
-# (sched, chunk, teams, threads) on the 4096 x 4096 grid: the worksharing
-# step's six schedules at the shapes its table gives them, then forms the step
-# does not use
-STENCIL_CHAIN = [
-    (CH, 1, 4096, 512), (CH, 8, 4096, 512), (CH, 64, 4096, 64), (ST, 0, 4096, 512),
-    (DY, 256, 2048, 32), (AU, 0, 1216, 1024),
+# the worksharing step's six schedules, with the (teams, threads) of the
+# committed tuning table (4 teams a SM x 256 threads where it has none)
+SCHED6 = [("static1", CH, 1), ("static8", CH, 8), ("static64", CH, 64), ("static", ST, 0),
+          ("dynamic256", DY, 256), ("auto", AU, 0)]
+
+
+def step_shape(body, label):
+    from paper_2106_03219_gb300 import autotune
+    table = autotune.load_sweep_table() or {}
+    return tuple(table.get("%s/%s" % (body, label), (4 * 152, 256)))
+
+
+# (sched, chunk, teams, threads) on the 4096 x 4096 grid: the step's six
+# schedules, then forms the step does not use
+STENCIL_CHAIN = [(sched, chunk) + step_shape("stencil2d", label)
+                 for label, sched, chunk in SCHED6] + [
     (DY, 64, 1024, 128), (CH, 4, 512, 256), (CH, 3, 1000, 96), (GU, 16, 300, 128),
     (DY, 256, 4096, 256), (CH, 32, 2048, 128), (AU, 0, 152, 256), (ST, 0, 333, 160),
 ]
@@ -116,21 +126,17 @@ def test_overlap_modes_agree_on_the_step(overlap_modes):
     x = inputs.f32_uniform01(n, 0)
     y0 = inputs.f32_uniform01(n, 1)
     g = inputs.grid_f32(4096, 4096, 0)
-    sched6 = [(CH, 1), (CH, 8), (CH, 64), (ST, 0), (DY, 256), (AU, 0)]
-    shapes = {"axpy": [(16384, 128), (8192, 256), (8192, 128), (8192, 512), (8192, 32),
-                       (16384, 256)],
-              "st": [(4096, 512), (4096, 512), (4096, 64), (4096, 512), (2048, 32), (1216, 1024)]}
     outs = []
     for on in (True, False):
         rt.set_launch_overlap(on)
         xd, yd, gd = dev(x), dev(y0), dev(g)
         od = torch.empty_like(gd)
         torch.cuda.synchronize()
-        for i, (sched, chunk) in enumerate(sched6):
-            G, T = shapes["axpy"][i]
+        for i, (label, sched, chunk) in enumerate(SCHED6):
+            G, T = step_shape("axpy", label)
             rt.launch_region(R.loop_desc(R.BODY_AXPY, n=n, x=xd, y=yd, alpha=3.0), sched, chunk,
                              G, T)
-            G, T = shapes["st"][i]
+            G, T = step_shape("stencil2d", label)
             src, dst = (gd, od) if i % 2 == 0 else (od, gd)
             rt.launch_region(R.loop_desc(R.BODY_STENCIL2D5, n=4096 * 4096, x=src, out=dst,
                                          nx=4096, ny=4096), sched, chunk, G, T)
@@ -138,7 +144,7 @@ def test_overlap_modes_agree_on_the_step(overlap_modes):
         del xd, yd, gd, od
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     want, want_y = g, y0
-    for _ in sched6:
+    for _ in SCHED6:
         want = O.stencil2d5(want)
         want_y = O.axpy_f32(3.0, x, want_y)
     assert np.array_equal(outs[0][1], bits32(want))
