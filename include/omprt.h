@@ -410,13 +410,13 @@ int32_t omprt_sm_count(const omprt_ctx *ctx);
  * routine.
  *  - The first call on a device looks up the array's device address for
  *    that device (cudaGetSymbolAddress, with that device current) and keeps
- *    it for the life of the process; make that first call before any stream
- *    capture.  The kept address is invalid after cudaDeviceReset on that
- *    device: do not call this entry point after such a reset.
+ *    it for the life of the process.  The kept address is invalid after
+ *    cudaDeviceReset on that device: do not call this entry point after
+ *    such a reset.
  *  - Every call shares the one array and clears its ticket on `stream`
- *    before launching, so calls that overlap on the GPU (different streams,
- *    or the same scratch used by two graphs running at once) race and give
- *    wrong results.  Calls ordered on one stream are safe.
+ *    before launching, so calls that overlap on the GPU (on different
+ *    streams) race and give wrong results.  Calls ordered on one stream are
+ *    safe.
  *  - The array keeps the last call's partials; nothing reads them later.
  *  - No device status word is reported, and none is needed: the team stack
  *    is fixed at 4 KiB, which always holds the call's 512 bytes of
