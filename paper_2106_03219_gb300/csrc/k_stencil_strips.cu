@@ -11,8 +11,9 @@
 // restarts at each block, which starts a row.)  In every row the thread's
 // iterations are its strips' points from left to right, and its next
 // iterations are the same columns one row down, so the thread walks its
-// strips down the rows in exactly the order OpenMP gives it (monotonic), with
-// the rows above, at and below in registers: each step loads one new row of
+// strips down the rows (the CTAs of even index in exactly the order OpenMP
+// gives it, those of odd index bottom up, see below), with the rows above,
+// at and below in registers: each step loads one new row of
 // its strips (the row after next, one step ahead) and takes the column west /
 // east of each strip from the neighbouring lane by shuffle (the lane beyond a
 // warp's edge loads it).  A warp's loads and stores cover contiguous memory.
@@ -87,22 +88,38 @@ __global__ void __launch_bounds__(1024) stencil2d_strips_kernel(const StripArgs 
   uint32_t col[M];  // first column of each strip
 #pragma unroll
   for (int m = 0; m < M; ++m) col[m] = (uint32_t)W * (t + (uint32_t)m * T);
-  // v[0] the row above, v[1] the row being computed, v[2 ..] the rows below
+  // Odd CTAs walk their band bottom up.  A row on the boundary of two bands
+  // is read by both CTAs; with the walks in opposite directions both reads
+  // come at the start of the two walks or both at the end, so the second
+  // finds the row still in L2 (top-down walks read it a whole band apart,
+  // after the L2 has turned over: 2 rows a band from DRAM again, 14% of the
+  // input at 4096^2).  A thread's iterations are independent, so the order
+  // of its rows is not observable.  (n < 2^32 and nx >= 32 keep rows in int.)
+  const int dir = (k & 1u) ? -1 : 1;
+  const int first = dir > 0 ? (int)R0 : (int)R1 - 1;
+  // a row the band reads: inside the grid and at most one row beyond the band
+  auto readable = [&](int r) {
+    return r >= 0 && r < (int)ny && r >= (int)R0 - 1 && r <= (int)R1;
+  };
+  // v[0] the row behind (above when walking down), v[1] the row being
+  // computed, v[2 ..] the rows ahead
   float v[D + 2][M][W];
-  auto load_row = [&](uint32_t r, float (&x)[M][W]) {
+  auto load_row = [&](int r, float (&x)[M][W]) {
 #pragma unroll
     for (int m = 0; m < M; ++m) strip_load<W>(A.in + (size_t)r * nx + col[m], x[m]);
   };
-  if (R0 >= 1) load_row(R0 - 1, v[0]);
-  load_row(R0, v[1]);
+  if (readable(first - dir)) load_row(first - dir, v[0]);
+  load_row(first, v[1]);
 #pragma unroll
-  for (int d = 2; d < D + 2; ++d)  // rows R0 + 1 .. R0 + D, those the band reads
-    if (R0 + d - 1 < ny && R0 + d - 2 < R1) load_row(R0 + d - 1, v[d]);
-  for (uint32_t r = R0; r < R1; ++r) {
+  for (int d = 2; d < D + 2; ++d)  // the D rows ahead of the first, those the band reads
+    if (readable(first + (d - 1) * dir)) load_row(first + (d - 1) * dir, v[d]);
+  for (uint32_t i = 0; i < R1 - R0; ++i) {
+    const uint32_t r = (uint32_t)(first + (int)i * dir);
     float nxt[M][W];
-    // row r + 1 + D, needed D steps from now
-    const bool more = r + D < R1 && r + 1 + D < ny;
-    if (more) load_row(r + 1 + D, nxt);
+    // the row 1 + D ahead, needed D steps from now
+    const int ahead = (int)r + (1 + D) * dir;
+    const bool more = readable(ahead);
+    if (more) load_row(ahead, nxt);
     const bool inner = r >= 1 && r + 1 < ny;
     const size_t row = (size_t)r * nx;
 #pragma unroll
@@ -119,6 +136,7 @@ __global__ void __launch_bounds__(1024) stencil2d_strips_kernel(const StripArgs 
         const uint32_t cc = col[m] + q;
         const float ww = q > 0 ? v[1][m][q - 1] : w;
         const float ee = q + 1 < W ? v[1][m][q + 1] : e;
+        // behind + ahead is N + S in either direction (the sum commutes)
         o[q] = (inner && cc > 0 && cc + 1 < nx)
                    ? strip_point(A, v[0][m][q], v[2][m][q], ee, ww, v[1][m][q])
                    : v[1][m][q];
