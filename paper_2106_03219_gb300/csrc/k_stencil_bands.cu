@@ -17,7 +17,9 @@
 // launch has P <= G resident CTAs of T threads; CTA k plays the consecutive
 // teams [k G / P, (k + 1) G / P), the rows [R0, R1), its thread tt as thread
 // tt of each team (OpenMP does not make teams run at the same time).  Every
-// thread runs its own points in order.  Boundary rows and columns copy their
+// thread runs its own points band by band, each band's rows in order (the
+// bands in order in CTAs of even index, from the last in those of odd
+// index: below).  Boundary rows and columns copy their
 // input; the arithmetic is the body's fma(c1, (N+S)+(E+W), c0*C).
 #include "tensor_map.h"
 
@@ -80,11 +82,18 @@ __global__ void __launch_bounds__(1024) stencil2d_bands_kernel(
   if (R0 >= R1) return;  // uniform; never with P <= G
   const uint32_t nx = A.nx, ny = A.ny;
   const uint32_t nb = (R1 - R0 + Rb - 1) / Rb;
+  // Odd CTAs take their bands from the last to the first: the rows on the
+  // boundary of two CTAs' ranges are then read by both at about the same
+  // time (at the start of both, or at the end of both), so the second read
+  // hits in L2.  A thread's points are independent, so the order of its
+  // rows is not observable.
+  const bool rev = (k & 1u) != 0;
+  auto band_row = [&](uint32_t b) { return R0 + (rev ? nb - 1u - b : b) * Rb; };
   auto issue = [&](uint32_t b, uint32_t slot) {
     const uint32_t bar = bar0 + 8 * slot;
     mbar_expect_tx(bar, M * A.box_bytes);
     const uint32_t dst = buf0 + slot * wbytes;
-    const int y = (int)(R0 + b * Rb) - 1;
+    const int y = (int)band_row(b) - 1;
 #pragma unroll
     for (int m = 0; m < M; ++m)
       tma_load_2d(dst + m * sb, &map, (int)(32u * w + m * T) - 4, y, bar);
@@ -115,7 +124,7 @@ __global__ void __launch_bounds__(1024) stencil2d_bands_kernel(
       break;
     }
     phase ^= 1u << slot;
-    const uint32_t rb0 = R0 + b * Rb, rb1 = rb0 + Rb < R1 ? rb0 + Rb : R1;
+    const uint32_t rb0 = band_row(b), rb1 = rb0 + Rb < R1 ? rb0 + Rb : R1;
     // word 4 + l of box row 0 of strip 0; strip m is m sb further
     const uint32_t lw = buf0 + slot * wbytes + 4u * (4u + lane);
     float up[M], cu[M];

@@ -11,8 +11,9 @@
 // lane l chunk l.  The grid is read as a 3-D tensor (x: the c floats of a
 // chunk, y: the m chunks of a row, z: rows).  A launch has P <= G resident
 // CTAs; CTA k plays the consecutive teams [k G / P, (k + 1) G / P) with K
-// warps, warp gr playing teams gr, gr + K, ... (OpenMP does not make teams
-// run at the same time).  In round i the K warps play K consecutive teams,
+// warps, warp gr playing teams gr, gr + K, ... (counted from the first team
+// in CTAs of even index, by rounds from the last in those of odd index;
+// OpenMP does not make teams run at the same time).  In round i the K warps play K consecutive teams,
 // whose blocks stack up without gaps, so slab s of them (x in [32 s,
 // 32 s + 32)), for all K teams, with one row above and below, is one box:
 // 32 K + 2 m lines of 128 bytes, copied with the 128-byte swizzle.  A
@@ -75,7 +76,14 @@ __global__ void __launch_bounds__(1024) stencil2d_colring_kernel(
   __syncthreads();
   if (g0 >= g1) return;  // uniform; never with P <= G
   const uint32_t ns = A.ns, m = A.m;
-  const uint32_t nsteps = (g1 - g0 + K - 1) / K * ns;
+  const uint32_t nr = (g1 - g0 + K - 1) / K, nsteps = nr * ns;
+  // Odd CTAs play their rounds from the last to the first: the rows on the
+  // boundary of two CTAs' ranges are then read by both at about the same
+  // time (at the start of both, or at the end of both), so the second read
+  // hits in L2.  Teams do not run in any order OpenMP fixes, and a team's
+  // chunks are its own.
+  const bool rev = (k & 1u) != 0;
+  auto round_of = [&](uint32_t q) { return rev ? nr - 1u - q / ns : q / ns; };
   // step q = i ns + s: round i, slab s
   if (w == K) {  // the producer warp
     if (lane == 0) {
@@ -87,7 +95,7 @@ __global__ void __launch_bounds__(1024) stencil2d_colring_kernel(
           s_bad = 1;
           break;
         }
-        const uint32_t i = q / ns, s = q % ns;
+        const uint32_t i = round_of(q), s = q % ns;
         const uint32_t z = (g0 + i * K) * A.R;  // the first team's first row
         mbar_expect_tx(full0 + 8 * slot, A.box_bytes);
         tma_load_3d(bufs + slot * A.slab, &map, (int)(32u * s), 0, (int)z - 1, full0 + 8 * slot);
@@ -104,32 +112,43 @@ __global__ void __launch_bounds__(1024) stencil2d_colring_kernel(
   auto line_addr = [&](uint32_t bb, uint32_t L) { return (bb + 128u * L) | ((L & 7u) << 4); };
   // this lane's row and the slab's first column at step q
   auto place = [&](uint32_t q, uint32_t& g, uint32_t& row, uint32_t& colS) {
-    const uint32_t i = q / ns, s = q % ns;
+    const uint32_t i = round_of(q), s = q % ns;
     g = g0 + i * K + w;
     row = g * A.R + rr;
     colS = ch * A.c + 32u * s;
   };
-  auto halo = [&](uint32_t q, float& wl, float& er) {
+  // The east word of a slab that is not its chunk's last is word 0 of the
+  // chunk's next slab, read from global memory two steps ahead (about when
+  // that slab's box arrives).  The words across a chunk boundary come from
+  // the neighbouring lanes instead (lane l + 1 holds the next chunk of the
+  // row): read from global memory they would be fetched ns - 1 steps away
+  // from their boxes, after the L2 has turned over, 2 x 64 bytes a chunk
+  // again from DRAM.
+  auto halo = [&](uint32_t q, float& er) {
     uint32_t g, row, colS;
     place(q, g, row, colS);
-    if (g < g1) {
-      const size_t ro = (size_t)row * A.nx;
-      if (q % ns == 0 && colS > 0) wl = __ldg(A.in + ro + colS - 1);
-      if (colS + 32 < A.nx) er = __ldg(A.in + ro + colS + 32);
-    }
+    if (g < g1 && q % ns + 1 < ns) er = __ldg(A.in + (size_t)row * A.nx + colS + 32);
   };
-  // the west / east words two steps ahead: (wl, er) now, (wl1, er1) next
-  float wl = 0.f, er = 0.f, wl1 = 0.f, er1 = 0.f;
-  halo(0, wl, er);
-  if (nsteps > 1) halo(1, wl1, er1);
+  float er = 0.f, er1 = 0.f;  // the east words of this step and the next
+  halo(0, er);
+  if (nsteps > 1) halo(1, er1);
+  float wl = 0.f;      // the west word of the current unit
+  float e_last = 0.f;  // word 0 of the row's next chunk, for the chunk's last slab
+  // A chunk's first 32-byte sector waits for its first point's west word,
+  // lane l - 1's last word, at the chunk's last slab: that point's inputs
+  // and the sector's other seven outputs are held until then.
+  float d_n = 0.f, d_s = 0.f, d_e = 0.f, d_c = 0.f;
+  float d_o[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  bool d_copy = true;
+  float* d_po = nullptr;
   for (uint32_t q = 0; q < nsteps; ++q) {
-    const uint32_t slot = q % NB;
-    float wl_n = 0.f, er_n = 0.f;
-    if (q + 2 < nsteps) halo(q + 2, wl_n, er_n);
+    const uint32_t slot = q % NB, s = q % ns;
+    float er_n = 0.f;
+    if (q + 2 < nsteps) halo(q + 2, er_n);
     uint32_t g, row, colS;
     place(q, g, row, colS);
     bool mine = g < g1;
-    if (SCHED == kDynamic && mine && q % ns == 0) {
+    if (SCHED == kDynamic && mine && s == 0) {
       // the claim of the team's 32 chunks, at its first slab
       uint32_t b0 = 0;
       if (lane == 0) b0 = atomicAdd(&ctr[g - g0], 32u);
@@ -146,18 +165,25 @@ __global__ void __launch_bounds__(1024) stencil2d_colring_kernel(
       break;
     }
     const uint32_t bb = bufs + slot * A.slab;
+    const uint32_t qN = line_addr(bb, lN), qC = line_addr(bb, lC), qS = line_addr(bb, lS);
+    float4 c = lds128_at(qC);
+    // at a chunk's first slab: lane l + 1's first word is the east word of
+    // this lane's last slab (for the row's last chunk it is not used: the
+    // chunk ends at column nx - 1, copied)
+    if (s == 0) e_last = __shfl_down_sync(0xffffffffu, c.x, 1);
+    const float er_s = s + 1 < ns ? er : e_last;
     if (mine) {
-      const uint32_t qN = line_addr(bb, lN), qC = line_addr(bb, lC), qS = line_addr(bb, lS);
       const bool edge_row = row == 0 || row + 1 == A.ny;
       float* const po = A.out + (size_t)row * A.nx + colS;
-      float4 c = lds128_at(qC);
       float4 op;  // the even unit of a pair, stored with the odd one
 #pragma unroll
       for (uint32_t u = 0; u < 8; ++u) {
         const float4 cn = u < 7 ? lds128_at(qC ^ (16u * (u + 1))) : c;
         const float4 nn = lds128_at(qN ^ (16u * u)), ss = lds128_at(qS ^ (16u * u));
-        const float e = u < 7 ? cn.x : er;
+        const float e = u < 7 ? cn.x : er_s;
         float4 o;
+        // (at a chunk's first slab o.x is not used: that point is computed
+        // at the chunk's last slab, from the inputs kept here)
         o.x = slab_point(A.c0, A.c1, nn.x, ss.x, c.y, wl, c.x);
         o.y = slab_point(A.c0, A.c1, nn.y, ss.y, c.z, c.x, c.y);
         o.z = slab_point(A.c0, A.c1, nn.z, ss.z, c.w, c.y, c.z);
@@ -165,23 +191,51 @@ __global__ void __launch_bounds__(1024) stencil2d_colring_kernel(
         if (u == 0 && colS == 0) o.x = c.x;          // column 0
         if (u == 7 && colS + 32 == A.nx) o.w = c.w;  // column nx - 1
         if (edge_row) o = c;                         // rows 0 and ny - 1
+        if (s == 0 && u == 0) {
+          d_n = nn.x;
+          d_s = ss.x;
+          d_e = c.y;
+          d_c = c.x;
+          d_copy = edge_row || colS == 0;
+        }
         if (u & 1) {
-          const uint32_t r8[8] = {as_u(op.x), as_u(op.y), as_u(op.z), as_u(op.w),
-                                  as_u(o.x),  as_u(o.y),  as_u(o.z),  as_u(o.w)};
-          st8(po + 4 * (u - 1), r8);
+          if (s == 0 && u == 1) {  // the chunk's first sector: held
+            d_o[0] = op.y;
+            d_o[1] = op.z;
+            d_o[2] = op.w;
+            d_o[3] = o.x;
+            d_o[4] = o.y;
+            d_o[5] = o.z;
+            d_o[6] = o.w;
+            d_po = po;
+          } else {
+            const uint32_t r8[8] = {as_u(op.x), as_u(op.y), as_u(op.z), as_u(op.w),
+                                    as_u(o.x),  as_u(o.y),  as_u(o.z),  as_u(o.w)};
+            st8(po + 4 * (u - 1), r8);
+          }
         } else {
           op = o;
         }
-        wl = c.w;
+        wl = c.w;  // the next unit's west (the next slab's, within the chunk)
         c = cn;
       }
     }
+    if (s + 1 == ns) {
+      // wl is now this chunk's last word: lane l - 1's is the west word of
+      // this lane's first point (a lane holding a row's first chunk starts
+      // at column 0, copied)
+      const float wprev = __shfl_up_sync(0xffffffffu, wl, 1);
+      if (mine && d_po) {
+        const float o0 = d_copy ? d_c : slab_point(A.c0, A.c1, d_n, d_s, d_e, wprev, d_c);
+        const uint32_t r8[8] = {as_u(o0),     as_u(d_o[0]), as_u(d_o[1]), as_u(d_o[2]),
+                                as_u(d_o[3]), as_u(d_o[4]), as_u(d_o[5]), as_u(d_o[6])};
+        st8(d_po, r8);
+      }
+      d_po = nullptr;
+    }
     __syncwarp();  // every lane has read the buffer before the warp releases it
     if (lane == 0) mbar_arrive(empty0 + 8 * slot);
-    // the next slab of the same chunk takes its west from this one's last unit
-    if ((q + 1) % ns == 0) wl = wl1;
     er = er1;
-    wl1 = wl_n;
     er1 = er_n;
   }
 }

@@ -22,8 +22,9 @@
 // lanes compute the current one.  A launch has P <= G resident CTAs; CTA k
 // plays the consecutive teams [k G / P, (k + 1) G / P) (OpenMP does not make
 // teams run at the same time).  Its W warps form K = W / (T / 32) groups;
-// group gr plays the CTA's teams gr, gr + K, ... in turn, its warp i as
-// threads 32 i .. 32 i + 31 of the team.
+// group gr plays the CTA's teams gr, gr + K, ... in turn (counted from the
+// first team in CTAs of even index, from the last in those of odd index),
+// its warp i as threads 32 i .. 32 i + 31 of the team.
 //   static(c):  warp i's lanes run chunks j0 + l of the block for j0 = 32 i,
 //               32 i + T, ... (thread tt runs chunks tt, tt + T, ...: C2);
 //   dynamic(c): lane 0 claims 32 chunks with one atomic add on the team's
@@ -89,6 +90,13 @@ __global__ void __launch_bounds__(kSlabMaxWarps * 32, 1) stencil2d_slabs_kernel(
   const uint32_t P = gridDim.x, k = blockIdx.x;
   const uint32_t g0 = (uint32_t)((uint64_t)k * A.G / P);
   const uint32_t g1 = (uint32_t)((uint64_t)(k + 1) * A.G / P);
+  // Odd CTAs play their teams from the last to the first: the rows on the
+  // boundary of two CTAs' bands are then read by both at about the same
+  // time (at the start of both, or at the end of both), so the second read
+  // hits in L2.  Teams do not run in any order OpenMP fixes, and each team
+  // still claims its own chunks in increasing order.
+  const bool rev = (k & 1u) != 0;
+  auto team_of = [&](uint32_t g) { return rev ? g0 + g1 - 1u - g : g; };  // onto [g0, g1)
   if (SCHED == kDynamic)
     for (uint32_t i = t; i < g1 - g0; i += blockDim.x) ctr[i] = 0;
   const uint32_t bar0 = smem_addr(&bars[w][0]);
@@ -134,7 +142,7 @@ __global__ void __launch_bounds__(kSlabMaxWarps * 32, 1) stencil2d_slabs_kernel(
   // the box of an item: x = X s, y = the first chunk's place in its row,
   // z = the row above the first chunk's row
   auto issue = [&](const SlabItem& it, uint32_t b) {
-    const uint32_t row0 = it.g * A.R + it.j0 / m;
+    const uint32_t row0 = team_of(it.g) * A.R + it.j0 / m;
     const uint32_t y = m >= 32 ? it.j0 % m : 0u;
     mbar_expect_tx(bar0 + 8 * b, A.box_bytes);
     tma_load_3d(buf0 + b * A.slab, &map, (int)((uint32_t)X * it.s), (int)y, (int)row0 - 1,
@@ -144,7 +152,7 @@ __global__ void __launch_bounds__(kSlabMaxWarps * 32, 1) stencil2d_slabs_kernel(
   // whether the chunk is one of the block's
   const uint32_t rr = lane / mb, ch = lane - rr * mb;  // row within the group, chunk
   auto place = [&](const SlabItem& it, uint32_t& row, uint32_t& colS) {
-    row = it.g * A.R + it.j0 / m + rr;
+    row = team_of(it.g) * A.R + it.j0 / m + rr;
     colS = ((m >= 32 ? it.j0 % m : 0u) + ch) * A.c + (uint32_t)X * it.s;
     return it.j0 + lane < nch;
   };
