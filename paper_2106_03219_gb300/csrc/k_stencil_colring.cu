@@ -31,7 +31,9 @@
 
 namespace rt {
 
-constexpr uint32_t kColMaxWarps = 31;   // compute warps, with the producer warp 1024 threads
+// compute warps: with the producer warp 512 threads, so a thread may hold
+// 128 registers (the held first sector of a chunk would spill at 64)
+constexpr uint32_t kColMaxWarps = 15;
 constexpr uint32_t kColMaxNB = 4;
 constexpr uint32_t kColMaxTeams = 1024;  // a CTA's teams (dynamic counters)
 constexpr uint64_t kColWaitNs = 1000000000ull;  // 1 s: a step takes microseconds
@@ -51,7 +53,7 @@ struct ColArgs {
 };
 
 template <int SCHED>
-__global__ void __launch_bounds__(1024) stencil2d_colring_kernel(
+__global__ void __launch_bounds__((kColMaxWarps + 1) * 32, 1) stencil2d_colring_kernel(
     const __grid_constant__ CUtensorMap map, const ColArgs A) {
   enter_region_grid();
   __shared__ __align__(8) uint64_t full[kColMaxNB], empty[kColMaxNB];
@@ -272,7 +274,7 @@ cudaError_t launch_stencil2d_colring(const void* in, float* out, uint64_t nx, ui
                             ? (uint64_t)max_smem - fa.sharedSizeBytes - 1024
                             : 0;
   // K warps: NB boxes of 128 (32 K + 2 m) bytes (each rounded up to 1 KB)
-  // within the shared memory, at most 31 warps, at most 256 box rows
+  // within the shared memory, at most kColMaxWarps warps, at most 256 box rows
   auto slab_of = [&](uint64_t kk) { return (128 * (32 * kk + 2 * m) + 1023) / 1024 * 1024; };
   uint64_t K = 0;
   while (K + 1 <= kColMaxWarps && (K + 1) * R + 2 <= 256 && NB * slab_of(K + 1) <= room) ++K;
