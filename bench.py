@@ -430,6 +430,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the reduction and batched-region measurements")
+    ap.add_argument("--sets", type=int, default=1,
+                    help="--single: rotate the launches over this many copies of the buffers")
     ap.add_argument("--single", default=None,
                     help="profiling aid: only launch plan entries whose name contains this "
                          "(e.g. axpy/auto), or one of reduce/fp32, reduce/bf16, reduce/int64, "
@@ -475,7 +477,7 @@ def main():
         del x, y, grid, out, plan
         return run_single_extra(rt, R, torch, inputs, args)
     if args.single:
-        return run_single(rt, torch, plan, args)
+        return run_single(rt, torch, plan, args, launches, inputs)
     step_bytes = sum(b for _, b, *_ in plan)
 
     def new_events():
@@ -651,20 +653,40 @@ def run_single_extra(rt, R, torch, inputs, args):
     return 0
 
 
-def run_single(rt, torch, plan, args):
-    sel = [p for p in plan if p[0] == args.single] or [p for p in plan if args.single in p[0]]
-    if not sel:
+def run_single(rt, torch, plan, args, launches, inputs):
+    """--single NAME: the plan entries matching NAME, launched back to back.
+    With --sets S > 1 launch k uses copy k mod S of the buffers, so that a
+    launch's inputs were last touched S - 1 launches earlier (the steady state
+    of kernels_steady: the previous launch's output still dirty in L2)."""
+    names = [p[0] for p in plan]
+    idx = [i for i, n in enumerate(names) if n == args.single] or \
+        [i for i, n in enumerate(names) if args.single in n]
+    if not idx:
         raise SystemExit("no plan entry matches %r" % args.single)
+    plans = [plan]
+    for k in range(1, max(1, args.sets)):
+        xx = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 0)).cuda()
+        yy = torch.from_numpy(inputs.f32_uniform01(N_AXPY, 1)).cuda()
+        gg = torch.from_numpy(inputs.grid_f32(GRID, GRID, k)).cuda()
+        plans.append(launches(xx, yy, gg, torch.empty_like(gg)))
+    sel = [plan[i] for i in idx]
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        for name, _, desc, sched, chunk, G, T in sel:
+    count = [0]
+
+    def launch_all():
+        P = plans[count[0] % len(plans)]
+        count[0] += 1
+        for i in idx:
+            name, _, desc, sched, chunk, G, T = P[i]
             rt.launch_region(desc, sched, chunk, G, T, stream=stream)
+
+    for _ in range(args.warmup):
+        launch_all()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        for name, _, desc, sched, chunk, G, T in sel:
-            rt.launch_region(desc, sched, chunk, G, T, stream=stream)
+        launch_all()
     e1.record(stream)
     torch.cuda.synchronize()
     assert rt.sync_status() == 0
