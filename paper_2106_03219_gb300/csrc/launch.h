@@ -30,15 +30,31 @@ inline cudaError_t smem_optin(K kern, size_t dyn, size_t static_bytes) {
 // Launch overlap, per host thread: whether executor launches may overlap
 // the tail of the previous grid on their stream (programmatic stream
 // serialisation; on by default), the shared memory of one SM (0: unknown),
-// and the stream and dynamic shared memory of the last executor launch.  An
-// API call on a context sets the first two from the context for its duration
-// (OverlapScope).
+// and the dynamic shared memory of the last executor launch on each of the
+// last kStreams streams this thread launched on.  An API call on a context
+// sets the first two from the context for its duration (OverlapScope).
 struct OverlapState {
+  static constexpr int kStreams = 8;
   bool on = true;
   size_t smem_per_sm = 0;
-  cudaStream_t last_stream = nullptr;
-  size_t last_smem = 0;
-  bool any = false;
+  cudaStream_t stream[kStreams] = {};
+  size_t smem[kStreams] = {};
+  int used = 0, next = 0;  // entries filled; the one to replace next
+  int find(cudaStream_t st) const {
+    for (int i = 0; i < used; ++i)
+      if (stream[i] == st) return i;
+    return -1;
+  }
+  void record(cudaStream_t st, size_t bytes) {
+    int i = find(st);
+    if (i < 0) {
+      i = next;
+      next = (next + 1) % kStreams;
+      if (used < kStreams) ++used;
+      stream[i] = st;
+    }
+    smem[i] = bytes;
+  }
 };
 inline OverlapState& overlap_state() {
   thread_local OverlapState s;
@@ -75,9 +91,11 @@ constexpr size_t kOverlapSmemStep = 16 * 1024;
 inline bool overlap_this_launch(cudaStream_t st, size_t smem) {
   const OverlapState& s = overlap_state();
   if (!s.on) return false;
-  if (!s.any || s.last_stream != st) return true;
-  const bool can_share = s.smem_per_sm == 0 || s.last_smem + smem <= s.smem_per_sm;
-  return !(can_share && s.last_smem >= smem + kOverlapSmemStep);
+  const int i = s.find(st);
+  if (i < 0) return true;
+  const size_t last = s.smem[i];
+  const bool can_share = s.smem_per_sm == 0 || last + smem <= s.smem_per_sm;
+  return !(can_share && last >= smem + kOverlapSmemStep);
 }
 
 // Launch an executor kernel (one that starts with enter_region_grid).  The
@@ -100,10 +118,7 @@ inline cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, 
     cudaGetLastError();
     return e;
   }
-  OverlapState& s = overlap_state();
-  s.last_stream = st;
-  s.last_smem = smem;
-  s.any = true;
+  overlap_state().record(st, smem);
   return e;
 }
 
