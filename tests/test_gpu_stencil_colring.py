@@ -5,8 +5,11 @@ playing adjacent teams from one tensor copy a step (k_stencil_colring.cu).
 The form applies when T = 32, c is a multiple of 32, m = nx / c divides 32
 with m < 32, and ny / G = 32 / m; the same launches with m >= 32 (one-row
 blocks) take the per-warp slabs.  Results must be bit-exact against the
-oracle for one to many slabs a chunk, CTAs with fewer teams than warps (idle
-warps in the last round), every buffer count, and the full grid."""
+oracle for every m from 1 to 16 with one to many slabs a chunk (the words
+across a chunk boundary come from the neighbouring lanes, the chunk's first
+sector is stored at its last slab), CTAs with fewer teams than warps (idle
+warps in the last round), CTAs that play their rounds in reverse, every
+buffer count, and the full grid."""
 import numpy as np
 import pytest
 
@@ -30,7 +33,8 @@ def _run(rt, ad, ny, nx, sched, chunk, G, T):
 
 
 @pytest.mark.parametrize("nx,c", [(32, 32), (64, 32), (256, 64), (1024, 32), (1024, 64),
-                                  (1024, 256), (2048, 1024), (2048, 64), (4096, 128)])
+                                  (1024, 256), (2048, 1024), (2048, 64), (4096, 128),
+                                  (64, 64), (256, 256), (256, 32), (512, 64), (128, 32)])
 @pytest.mark.parametrize("G", [1, 2, 7, 40, 300])
 def test_colring_bit_exact(rt, nx, c, G):
     m = nx // c
